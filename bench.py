@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark: multilevel 2-D DWT by non-separable lifting on GB300.
+
+Workload (one step): CDF 9/7 forward transform of one 8192 x 8192 float32
+image, 5 levels, non-separable lifting in its reduced form, through the C ABI
+(dwt2d_forward), input resident in HBM.  The image (256 MiB) and the
+coefficients (256 MiB) are both larger than L2, so no flush is needed between
+steps.  Also measured in the same run and reported under "variants": every
+scheme (separable, non-separable, reduced, and their multipass forms) forward
+and inverse, and reversible LeGall 5/3 int32.
+
+Prints ONE JSON line.  `--impl reference` times the FP64 oracle on the host
+cores instead (a bounded sample of the same workload).
+Multi-GPU: one process per GPU (torchrun); every rank transforms its own image
+(replicas, no collective on the data path); value = all ranks' pixels / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "Gpixel/s and % HBM roofline, CDF 9/7 fwd 8192² 5 levels, non-sep vs separable"
+UNIT = "Gpixel/s"
+H = W = 8192
+LEVELS = 5
+HEADLINE_SCHEME = "nonsep_reduced"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash() -> str:
+    """Short hash of the kernel sources (a profile taken on other sources is stale)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1705_08266_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kernel_tag: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary.
+
+    The summary line reads `traffic_bytes_per_launch: <bytes> <kernel tag> src=<hash>`;
+    None if absent, for another kernel, or taken on different kernel sources.
+    """
+    path = os.path.join(ROOT, "profiles", "fwd_fused_cdf97_8192x8192_l5.md")
+    try:
+        with open(path) as f:
+            for line in f:
+                if not line.startswith("traffic_bytes_per_launch:"):
+                    continue
+                parts = line.split(":", 1)[1].split()
+                if len(parts) >= 3 and parts[1] == kernel_tag and parts[2] == "src=" + kernel_source_hash():
+                    return float(parts[0])
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled in the background."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.f = open(self.path, "w")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self, t0: float, t1: float):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                    rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+                except (ValueError, IndexError):
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05] or rows[-3:]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+def time_calls(fn, iters: int, stream) -> float:
+    """Mean ms per call of fn() on `stream`, CUDA events, after the caller's warm-up."""
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record(stream)
+    for _ in range(iters):
+        fn()
+    e.record(stream)
+    e.synchronize()
+    return s.elapsed_time(e) / iters
+
+
+def cpu_baseline(seconds_hint: float = 15.0):
+    """The FP64 oracle timed on this host on a bounded sample of the workload."""
+    from oracle import lifting as L
+    from paper_1705_08266_gb300 import synth
+
+    n = H  # the full workload image: about 10-30 s of single-thread FP64 work
+    x = synth.gradient_noise(n, n, synth.SEED_LARGE)
+    t0 = time.perf_counter()
+    runs = 0
+    while True:
+        L.forward(x, LEVELS, "cdf97")
+        runs += 1
+        if time.perf_counter() - t0 > seconds_hint or runs >= 3:
+            break
+    dt = (time.perf_counter() - t0) / runs
+    return {"value": round(n * n / dt / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"CDF 9/7 forward, {n}x{n} of the same gradient+noise recipe, {LEVELS} levels, "
+                      f"FP64 numpy separable lifting, single thread, mean of {runs} run(s)"}
+
+
+def run_reference(args, ws, rank):
+    """--impl reference: the FP64 oracle on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    from oracle import lifting as L
+    from paper_1705_08266_gb300 import synth
+
+    n = 2048  # 1/16 of the workload's pixels per step, so K steps end within minutes
+    x = synth.gradient_noise(n, n, synth.SEED_LARGE)
+    for _ in range(min(max(args.warmup, 0), 3)):
+        L.forward(x, LEVELS, "cdf97")
+    steps = max(args.steps, 1)
+    budget = 150.0
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(steps):
+        L.forward(x, LEVELS, "cdf97")
+        done += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = (time.perf_counter() - t0) / done
+    v = n * n / dt / 1e9
+    sample = (f"CDF 9/7 forward of a {n}x{n} crop-size image of the same recipe, {LEVELS} levels, "
+              f"FP64 numpy oracle, single thread; {done} timed step(s)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": done, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"CDF 9/7 forward, {n}x{n} float64 oracle sample, {LEVELS} levels",
+                   "parallelism": "host, 1 thread"},
+        "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    from paper_1705_08266_gb300 import dwt2d as D
+    from paper_1705_08266_gb300 import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    x_h = synth.gradient_noise(H, W, synth.SEED_LARGE)
+    x = D.empty_image(H, W, torch.float32, dev)
+    x.copy_(torch.from_numpy(x_h))
+    dst = D.empty_image(H, W, torch.float32, dev)
+    plan = D.Plan(H, W, LEVELS, "cdf97", HEADLINE_SCHEME)
+    wsb = plan.workspace(dev)
+    launches, fused = plan.info()
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+
+    fwd = lambda: plan.forward(x, dst, wsb, stream=stream)  # noqa: E731
+    for _ in range(max(args.warmup, 3)):
+        fwd()
+    torch.cuda.synchronize()
+
+    # per-launch events of every timed step (dominant kernel = launch 0)
+    K = max(args.steps, 1)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * launches)] for _ in range(K)]
+    for row in evs:  # torch creates an event on its first record; the library re-records it
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    start.record(stream)
+    for k in range(K):
+        plan.set_launch_events(evs[k])
+        fwd()
+    end.record(stream)
+    end.synchronize()
+    t1 = time.time()
+    torch.cuda.synchronize()
+    barrier(ws)
+    plan.set_launch_events(None)
+    clocks = sampler.stop(t0, t1)
+    ms_local = start.elapsed_time(end) / K
+    ms = max_over_ranks(ws, ms_local)
+    assert plan.status(wsb) == 0, "kernel reported a timeout"
+
+    launch_ms = [statistics.mean(evs[k][2 * i].elapsed_time(evs[k][2 * i + 1]) for k in range(K))
+                 for i in range(launches)]
+    dom = int(np.argmax(launch_ms))
+    value = ws * H * W / (ms / 1e3) / 1e9
+
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # dominant launch: fused levels 1..fused[0] of the full image: reads the image once and
+    # writes every coefficient of those levels (details + LL) once = 2 * 4 * H * W bytes
+    alg_bytes_dom = 2 * 4 * H * W if dom == 0 else None
+    strict_bytes = 2 * 4 * H * W  # the whole transform: image read once, coefficients written once
+    traffic = profiled_traffic(f"fused{fused[0]}")
+    achieved = alg_bytes_dom / (launch_ms[dom] / 1e3) / 1e9 if alg_bytes_dom else None
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": hbm,
+                "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
+                "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": f"fwd_fused_kernel<float, nonsep_reduced, {fused[0]}> (launch {dom})",
+                "kernel_ms": round(launch_ms[dom], 5),
+                "alg_bytes_per_launch": alg_bytes_dom,
+                "whole_step": {"strict_bytes": strict_bytes,
+                               "achieved": round(strict_bytes / (ms / 1e3) / 1e9, 1),
+                               "frac": round(strict_bytes / (ms / 1e3) / 1e9 / hbm, 4)}}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "CDF 9/7 forward, 8192x8192 float32, 5 levels, non-separable lifting "
+                               "(reduced form), input resident in HBM",
+                   "image": [H, W], "levels": LEVELS, "wavelet": "cdf97", "scheme": HEADLINE_SCHEME,
+                   "launches_per_step": launches, "fused_levels_per_launch": fused,
+                   "l2": "inputs and outputs (256 MiB each) larger than L2; no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "gpu_launches": launches * K,
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+
+    if not args.no_variants:
+        out["variants"] = variants(D, synth, dev, stream, x, dst)
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    hs = torch.from_numpy(x_h).pin_memory()
+    hd = torch.empty_like(hs).pin_memory()
+    din = D.empty_image(H, W, torch.float32, dev)
+    for _ in range(2):
+        plan.forward_host(hs, hd, din, dst, wsb, stream=stream)
+    n_e2e = min(K, 30)
+    barrier(ws)
+    te = time.perf_counter()
+    for _ in range(n_e2e):
+        plan.forward_host(hs, hd, din, dst, wsb, stream=stream)
+    e2e_s = max_over_ranks(ws, (time.perf_counter() - te) / n_e2e)
+    out["e2e"] = {"value": round(ws * H * W / e2e_s / 1e9, 3), "unit": UNIT,
+                  "h2d_bytes_per_step": 4 * H * W, "d2h_bytes_per_step": 4 * H * W,
+                  "steps": n_e2e, "api": "dwt2d_forward_host (pinned host buffers)"}
+    out["gpu_launches"] += launches * (n_e2e + 2)
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def variants(D, synth, dev, stream, x, dst):
+    """Every scheme forward / inverse (9/7) and 5/3, same image size."""
+    res = {}
+    iters, warm = 20, 3
+    strict = 2 * 4 * H * W
+    hbm = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+    c = D.empty_image(H, W, torch.float32, dev)
+    for scheme in D.SCHEMES:
+        plan = D.Plan(H, W, LEVELS, "cdf97", scheme)
+        wsb = plan.workspace(dev)
+        plan.forward(x, c, wsb, stream=stream)
+        for direction, fn in (("fwd", lambda: plan.forward(x, c, wsb, stream=stream)),
+                              ("inv", lambda: plan.inverse(c, dst, wsb, stream=stream))):
+            for _ in range(warm):
+                fn()
+            ms = time_calls(fn, iters, stream)
+            res[f"cdf97_f32_{scheme}_{direction}"] = {
+                "ms": round(ms, 5), "gpx_s": round(H * W / ms / 1e6, 2),
+                "strict_frac": round(strict / (ms / 1e3) / 1e9 / hbm, 4),
+                "launches": plan.info()[0]}
+        del wsb
+    xi = D.empty_image(H, W, torch.int32, dev)
+    xi.copy_(torch.from_numpy(synth.uniform_int(H, W, synth.SEED_LARGE)))
+    ci = D.empty_image(H, W, torch.int32, dev)
+    yi = D.empty_image(H, W, torch.int32, dev)
+    for scheme in ("separable", "nonsep", "separable_multipass", "nonsep_multipass"):
+        plan = D.Plan(H, W, LEVELS, "legall53", scheme)
+        wsb = plan.workspace(dev)
+        plan.forward(xi, ci, wsb, stream=stream)
+        for direction, fn in (("fwd", lambda: plan.forward(xi, ci, wsb, stream=stream)),
+                              ("inv", lambda: plan.inverse(ci, yi, wsb, stream=stream))):
+            for _ in range(warm):
+                fn()
+            ms = time_calls(fn, iters, stream)
+            res[f"legall53_i32_{scheme}_{direction}"] = {
+                "ms": round(ms, 5), "gpx_s": round(H * W / ms / 1e6, 2),
+                "strict_frac": round(strict / (ms / 1e3) / 1e9 / hbm, 4),
+                "launches": plan.info()[0]}
+    return res
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * dwt2d.h -- C ABI of a GB300 (sm_103a) library for the multilevel 2-D discrete
+ * wavelet transform computed by lifting, in the separable and non-separable
+ * forms of Barina et al., "Accelerating Discrete Wavelet Transforms on GPUs"
+ * (arXiv 1705.08266).
+ *
+ * What is computed
+ * ----------------
+ * One level splits an H x W image into four bands (Sec. 2: the 2-D transform
+ * is the tensor product of 1-D transforms and yields a quadruple of
+ * coefficients).  With quadruple (r, c) = (x[2r][2c], x[2r][2c+1],
+ * x[2r+1][2c], x[2r+1][2c+1]) = (c0, c1, c2, c3):
+ *   c0 -> LL, c1 -> HL (high pass along rows), c2 -> LH, c3 -> HH.
+ * Bands are stored in the Mallat layout: LL is the top-left ceil(H/2) x
+ * ceil(W/2) block, HL top-right, LH bottom-left, HH bottom-right.  Level l+1
+ * transforms the LL of level l (multi-scale Mallat recursion; the paper
+ * treats one scale and names more as future work, Sec. 5).
+ *
+ * Lifting (Sec. 2, Eq. 2): per (predict P, update U) pair, the separable
+ * scheme runs T_P^H, T_P^V, S_U^H, S_U^V (four barrier steps); the
+ * non-separable scheme (Sec. 3) runs the spatial predict T_P and the spatial
+ * update S_U (two steps); the reduced form (Sec. 3, P = P0 + P1, U = U0 + U1)
+ * computes the same two steps with fewer multiply-accumulates.  CDF 9/7 uses
+ * two pairs and a final scaling low / K, high * K per axis
+ * (K = 1.230174104914001); reversible LeGall 5/3 uses one integer pair
+ * d = x_odd - floor((e_i + e_{i+1})/2), s = x_even + floor((d_{i-1} + d_i + 2)/4),
+ * applied in the order T^H, T^V, S^H, S^V, which every scheme reproduces
+ * bit for bit.  Borders use whole-sample symmetric extension; an axis of
+ * length 1 is left unchanged.
+ *
+ * Schemes ending in _MULTIPASS run every lifting step as its own kernel that
+ * exchanges all coefficients through HBM: the GB300 restatement of the paper's
+ * pixel-shader mapping, in which results are exchanged through off-chip
+ * textures and nothing stays in registers (Sec. 3, last paragraphs).  The
+ * other schemes keep a level's data on chip: tiles staged by TMA, lifting in
+ * registers with warp shuffles, several levels fused per launch.
+ *
+ * Conventions
+ * -----------
+ * - Every pointer named d_* is a device pointer of the current device; the
+ *   caller allocates and owns all device memory and the stream.  The library
+ *   never allocates device memory, never synchronizes a stream (except the
+ *   *_host calls and dwt2d_workspace_status, which say so), never prints and
+ *   never aborts.
+ * - Pitches are in bytes, must be multiples of 16 and at least width *
+ *   element size; device base pointers must be 16-byte aligned
+ *   (DWT2D_ERR_ALIGN otherwise).
+ * - Element types: DWT2D_F32 (CDF 9/7), DWT2D_I32 (LeGall 5/3),
+ *   DWT2D_F16 / DWT2D_BF16 (CDF 9/7 with 16-bit storage, FP32 arithmetic,
+ *   stored value = coefficient / scale).  Other pairs: DWT2D_ERR_UNSUPPORTED.
+ * - src and dst must not overlap.  Launch errors return DWT2D_ERR_CUDA; a
+ *   kernel that gives up waiting on a copy (bounded waits) records
+ *   DWT2D_ERR_TIMEOUT in the workspace, read by dwt2d_workspace_status.
+ */
+#ifndef DWT2D_H
+#define DWT2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dwt2d_plan_s* dwt2d_plan_t; /* opaque, host memory, owned by the caller */
+
+typedef enum { DWT2D_CDF97 = 0, DWT2D_LEGALL53 = 1 } dwt2d_wavelet;
+
+typedef enum {
+    DWT2D_SEPARABLE = 0,            /* S_U^V | S_U^H | T_P^V | T_P^H per pair (Sec. 2) */
+    DWT2D_NONSEP = 1,               /* S_U | T_P, plain matrices (Sec. 3)              */
+    DWT2D_NONSEP_REDUCED = 2,       /* S_U | T_P with P = P0 + P1, U = U0 + U1 (Sec. 3) */
+    DWT2D_SEPARABLE_MULTIPASS = 3,  /* one HBM round trip per step (shader mapping)    */
+    DWT2D_NONSEP_MULTIPASS = 4,
+    DWT2D_NONSEP_REDUCED_MULTIPASS = 5
+} dwt2d_scheme;
+
+typedef enum { DWT2D_F32 = 0, DWT2D_I32 = 1, DWT2D_F16 = 2, DWT2D_BF16 = 3 } dwt2d_dtype;
+
+typedef enum { DWT2D_SYMMETRIC_WHOLE = 0 } dwt2d_boundary;
+
+typedef enum {
+    DWT2D_OK = 0,
+    DWT2D_ERR_INVALID = -1,     /* bad argument (null pointer, size, level count) */
+    DWT2D_ERR_UNSUPPORTED = -2, /* wavelet / dtype / scheme combination not offered */
+    DWT2D_ERR_ALIGN = -3,       /* pointer or pitch alignment */
+    DWT2D_ERR_NOMEM = -4,       /* host allocation of the plan failed */
+    DWT2D_ERR_CUDA = -5,        /* a CUDA call or launch failed */
+    DWT2D_ERR_TIMEOUT = -6      /* a kernel gave up a bounded wait */
+} dwt2d_status;
+
+/*
+ * dwt2d_plan -- validate a transform description and build a host plan.
+ *   Problem statement: Sec. 2 (single-scale 2-D DWT of an image by lifting,
+ *   Eq. 2) and Sec. 3 (non-separable scheme); levels > 1 is the Mallat
+ *   recursion on LL.
+ *   out             receives the plan (free with dwt2d_plan_destroy).
+ *   height, width   image size, >= 1 each, at most 65536 each.
+ *   levels          1 .. 16.
+ *   workspace_bytes receives the size of the device workspace that every
+ *                   forward / inverse call on this plan needs (>= 256).  The
+ *                   workspace must be zeroed once before first use
+ *                   (dwt2d_workspace_init); one workspace must not be used by
+ *                   two calls that run at the same time.
+ *   Errors: DWT2D_ERR_INVALID, DWT2D_ERR_UNSUPPORTED, DWT2D_ERR_NOMEM.
+ *   The plan is immutable; concurrent calls on different streams with
+ *   different workspaces may share it.
+ */
+dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,
+                        dwt2d_wavelet wavelet, dwt2d_scheme scheme, dwt2d_boundary boundary,
+                        dwt2d_dtype dtype, size_t* workspace_bytes);
+
+/*
+ * dwt2d_forward -- image -> Mallat-layout coefficients (Sec. 2 and Sec. 3).
+ *   d_src           height x width elements of the plan's dtype, row pitch
+ *                   src_pitch_bytes.  Not modified.
+ *   d_dst           height x width coefficients, row pitch dst_pitch_bytes.
+ *   d_workspace     workspace_bytes from dwt2d_plan (device, 16-byte aligned).
+ *   scale           16-bit storage only: stored value = value / scale, for
+ *                   input and coefficients alike (> 0); ignored otherwise.
+ *   stream          a cudaStream_t (NULL = legacy default stream).
+ *   Asynchronous on stream.  Errors: DWT2D_ERR_INVALID, DWT2D_ERR_ALIGN,
+ *   DWT2D_ERR_CUDA.
+ */
+dwt2d_status dwt2d_forward(dwt2d_plan_t plan, const void* d_src, int64_t src_pitch_bytes,
+                           void* d_dst, int64_t dst_pitch_bytes, void* d_workspace,
+                           float scale, void* stream);
+
+/*
+ * dwt2d_inverse -- Mallat-layout coefficients -> image: the inverse of Eq. 2,
+ *   every lifting step undone in reverse order (negated filters; the integer
+ *   5/3 steps undone exactly), coarse levels first.  Arguments as
+ *   dwt2d_forward, with d_src the coefficients and d_dst the image.
+ */
+dwt2d_status dwt2d_inverse(dwt2d_plan_t plan, const void* d_src, int64_t src_pitch_bytes,
+                           void* d_dst, int64_t dst_pitch_bytes, void* d_workspace,
+                           float scale, void* stream);
+
+/*
+ * dwt2d_forward_host / dwt2d_inverse_host -- the same transform on HOST
+ *   buffers: copies h_src (host, pitch h_src_pitch_bytes; pinned memory for
+ *   overlap) into d_stage_in, transforms into d_stage_out, copies d_stage_out
+ *   back to h_dst, all on stream, then synchronizes stream.
+ *   d_stage_in, d_stage_out: device buffers of height rows x d_pitch_bytes.
+ *   Errors: as dwt2d_forward, plus DWT2D_ERR_CUDA for a failed copy.
+ */
+dwt2d_status dwt2d_forward_host(dwt2d_plan_t plan, const void* h_src, int64_t h_src_pitch_bytes,
+                                void* h_dst, int64_t h_dst_pitch_bytes, void* d_stage_in,
+                                void* d_stage_out, int64_t d_pitch_bytes, void* d_workspace,
+                                float scale, void* stream);
+dwt2d_status dwt2d_inverse_host(dwt2d_plan_t plan, const void* h_src, int64_t h_src_pitch_bytes,
+                                void* h_dst, int64_t h_dst_pitch_bytes, void* d_stage_in,
+                                void* d_stage_out, int64_t d_pitch_bytes, void* d_workspace,
+                                float scale, void* stream);
+
+/*
+ * dwt2d_workspace_init -- zero the status word of a workspace (asynchronous on
+ *   stream).  Call once after allocating a workspace.
+ * dwt2d_workspace_status -- copy the status word to the host (synchronizes
+ *   stream), reset it to zero, and return DWT2D_OK or the recorded error
+ *   (DWT2D_ERR_TIMEOUT).
+ */
+dwt2d_status dwt2d_workspace_init(void* d_workspace, void* stream);
+dwt2d_status dwt2d_workspace_status(void* d_workspace, void* stream);
+
+/*
+ * dwt2d_plan_info -- kernel launches one forward call makes (for launch
+ *   accounting), and the number of levels fused per launch, in launch order.
+ *   fused: array of at least 16 entries (may be NULL).
+ */
+dwt2d_status dwt2d_plan_info(dwt2d_plan_t plan, int32_t* launches_per_call, int32_t* fused,
+                             int32_t* n_groups);
+
+/*
+ * dwt2d_plan_set_launch_events -- profiling hook.  With events != NULL, every
+ *   later forward / inverse call on this plan records events[2i] (a
+ *   cudaEvent_t) on its stream just before its i-th kernel launch and
+ *   events[2i+1] just after it, for i < count.  NULL turns the hook off.  The
+ *   caller owns the events.  Not safe while another call uses the plan.
+ */
+dwt2d_status dwt2d_plan_set_launch_events(dwt2d_plan_t plan, void** events, int32_t count);
+
+void dwt2d_plan_destroy(dwt2d_plan_t plan);
+const char* dwt2d_status_string(dwt2d_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DWT2D_H */

@@ -1,0 +1,589 @@
+// C ABI of the library: plans, workspace layout, level grouping, dispatch.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "dwt2d.h"
+#include "dwt_internal.h"
+
+using namespace dwt;
+
+namespace {
+
+constexpr size_t kHeader = 256;  // status word + padding at the start of the workspace
+
+struct Group {
+    int first;  // first level of the group (0-based)
+    int n;      // levels fused
+};
+
+}  // namespace
+
+struct dwt2d_plan_s {
+    int H, W, levels;
+    dwt2d_wavelet wavelet;
+    dwt2d_scheme scheme;
+    dwt2d_dtype dtype;
+    int elem;         // bytes per element
+    int hs[17], ws[17];  // extent transformed by level l (l = 0 .. levels-1)
+    Group groups[16];
+    int ngroups;
+    int sm_count;
+    int fwd_warps_target, inv_warps_target;
+    int min_segq;
+    // workspace layout (bytes from the start of the workspace)
+    size_t off_a, off_b, off_x, off_y;
+    long long pitch_a, pitch_b, pitch_x;  // elements
+    size_t ws_bytes;
+    // profiling hook: events[2i] / events[2i+1] around launch i
+    cudaEvent_t* events;
+    int nevents;
+};
+
+namespace {
+
+long long round_pitch(long long w, int elem) {
+    const long long bytes = (w * elem + 15) / 16 * 16;
+    return bytes / elem;
+}
+
+bool multipass(dwt2d_scheme s) { return s >= DWT2D_SEPARABLE_MULTIPASS; }
+
+int base_scheme(dwt2d_scheme s) {
+    switch (s) {
+        case DWT2D_SEPARABLE:
+        case DWT2D_SEPARABLE_MULTIPASS: return SCH_SEP;
+        case DWT2D_NONSEP:
+        case DWT2D_NONSEP_MULTIPASS: return SCH_NONSEP;
+        default: return SCH_RED;
+    }
+}
+
+int env_int(const char* name, int dflt) {
+    const char* v = getenv(name);
+    if (!v || !*v) return dflt;
+    return atoi(v);
+}
+
+void level_scale(int h, int w, bool inverse, float s[4]) {
+    const double K = 1.230174104914001;
+    const double kh = w > 1 ? K : 1.0, kv = h > 1 ? K : 1.0;
+    const double f[4] = {1.0 / (kh * kv), kh / kv, kv / kh, kh * kv};
+    for (int k = 0; k < 4; ++k) s[k] = (float)(inverse ? 1.0 / f[k] : f[k]);
+}
+
+// Lanes whose every column at the deepest fused level is valid, for a warp of
+// 32 lanes x 4 level-1 quadruple columns and a lifting radius rho (quadruples).
+void valid_lanes(int nl, int rho, int* lo_out, int* hi_out) {
+    int lo = rho, hi = 128 - rho;  // level-1 valid quadruple columns [lo, hi)
+    for (int l = 2; l <= nl; ++l) {
+        const int nlo = (lo + 2 * rho + 1) / 2;          // ceil((lo + 2 rho) / 2)
+        const int nhi = (hi - 2 - 2 * rho) / 2 + 1;      // floor((hi - 2 - 2 rho) / 2) + 1
+        lo = nlo;
+        hi = nhi;
+    }
+    const int q = 4 >> (nl - 1);
+    int llo = 32, lhi = 0;
+    for (int l = 0; l < 32; ++l) {
+        if (l * q >= lo && l * q + q <= hi) {
+            if (l < llo) llo = l;
+            lhi = l + 1;
+        }
+    }
+    *lo_out = llo;
+    *hi_out = lhi;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+dwt2d_status make_map(CUtensorMap* map, const void* base, int h, int w, long long pitch_elems,
+                      int elem, bool is_int) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return DWT2D_ERR_CUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
+    const cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * elem)};
+    const cuuint32_t box[2] = {(cuuint32_t)kBoxW, (cuuint32_t)kFwdSlotRows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, is_int ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                          2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? DWT2D_OK : DWT2D_ERR_CUDA;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+dwt2d_status check_buffers(const dwt2d_plan_s* p, const void* src, int64_t sp, const void* dst,
+                           int64_t dp, const void* ws) {
+    if (!p || !src || !dst || !ws) return DWT2D_ERR_INVALID;
+    if (!aligned16(src) || !aligned16(dst) || !aligned16(ws)) return DWT2D_ERR_ALIGN;
+    if (sp % 16 || dp % 16) return DWT2D_ERR_ALIGN;
+    const int64_t row = (int64_t)p->W * p->elem;
+    if (sp < row || dp < row) return DWT2D_ERR_INVALID;
+    return DWT2D_OK;
+}
+
+// Warp work decomposition of one streaming launch.
+void decompose(const dwt2d_plan_s* p, int w_first, int rows, int nl, int rho, int target_warps,
+               FusedArgs* a, int* grid, int warps_per_block) {
+    valid_lanes(nl, rho, &a->lane_lo, &a->lane_hi);
+    const int qn = 4 >> (nl - 1);
+    a->valid_px = (a->lane_hi - a->lane_lo) * qn * (1 << nl);
+    a->xoff = a->lane_lo * qn * (1 << nl);
+    a->nstrips = (w_first + a->valid_px - 1) / a->valid_px;
+    int nsegs = target_warps / a->nstrips;
+    if (nsegs < 1) nsegs = 1;
+    int segq = (rows + nsegs - 1) / nsegs;
+    if (segq < p->min_segq) segq = p->min_segq;
+    if (segq > rows) segq = rows;
+    if (segq < 1) segq = 1;
+    a->segq = segq;
+    a->nsegs = (rows + segq - 1) / segq;
+    const int items = a->nstrips * a->nsegs;
+    *grid = (items + warps_per_block - 1) / warps_per_block;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void mark(const dwt2d_plan_s* p, int launch, int side, cudaStream_t st) {
+    if (p->events && launch < p->nevents) cudaEventRecord(p->events[2 * launch + side], st);
+}
+
+dwt2d_status run_fused(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t sp, void* dst,
+                       int64_t dp, void* ws, cudaStream_t st) {
+    const int elem_kind = p->dtype == DWT2D_I32 ? 1 : 0;
+    const int rho = p->wavelet == DWT2D_CDF97 ? 2 : 1;
+    const int sch = base_scheme(p->scheme);
+    char* wsb = reinterpret_cast<char*>(ws);
+    int* err = reinterpret_cast<int*>(wsb);
+    void* bufs[2] = {wsb + p->off_a, wsb + p->off_b};
+    const long long bpitch[2] = {p->pitch_a, p->pitch_b};
+    const long long src_pe = sp / p->elem, dst_pe = dp / p->elem;
+
+    if (fwd) {
+        const void* in = src;
+        long long in_pitch = src_pe;
+        for (int gi = 0; gi < p->ngroups; ++gi) {
+            const Group g = p->groups[gi];
+            FusedArgs a;
+            memset(&a, 0, sizeof(a));
+            for (int i = 0; i < g.n; ++i) {
+                a.lv[i].h = p->hs[g.first + i];
+                a.lv[i].w = p->ws[g.first + i];
+                level_scale(a.lv[i].h, a.lv[i].w, false, a.lv[i].s);
+            }
+            a.mallat = dst;
+            a.mallat_pitch = dst_pe;
+            const bool last = gi == p->ngroups - 1;
+            a.ll = last ? dst : bufs[gi & 1];
+            a.ll_pitch = last ? dst_pe : bpitch[gi & 1];
+            a.err = err;
+            CUtensorMap map;
+            dwt2d_status s = make_map(&map, in, a.lv[0].h, a.lv[0].w, in_pitch, p->elem, elem_kind == 1);
+            if (s != DWT2D_OK) return s;
+            const int hN = a.lv[g.n - 1].h;
+            int grid;
+            decompose(p, a.lv[0].w, (hN + 1) / 2, g.n, rho, p->fwd_warps_target, &a, &grid, kFwdWarps);
+            mark(p, gi, 0, st);
+            if (launch_fwd_fused(elem_kind, sch, g.n, map, a, grid, st) != cudaSuccess)
+                return DWT2D_ERR_CUDA;
+            mark(p, gi, 1, st);
+            in = a.ll;
+            in_pitch = a.ll_pitch;
+        }
+        return DWT2D_OK;
+    }
+    // inverse: coarse group first
+    const void* ll_in = src;  // the coarsest LL sits at the top-left of the Mallat array
+    long long ll_pitch = src_pe;
+    for (int gi = p->ngroups - 1, k = 0; gi >= 0; --gi, ++k) {
+        const Group g = p->groups[gi];
+        FusedArgs a;
+        memset(&a, 0, sizeof(a));
+        for (int i = 0; i < g.n; ++i) {
+            a.lv[i].h = p->hs[g.first + i];
+            a.lv[i].w = p->ws[g.first + i];
+            level_scale(a.lv[i].h, a.lv[i].w, true, a.lv[i].s);
+        }
+        a.mallat = const_cast<void*>(src);
+        a.mallat_pitch = src_pe;
+        a.ll = const_cast<void*>(ll_in);
+        a.ll_pitch = ll_pitch;
+        const bool last = gi == 0;
+        a.out = last ? dst : bufs[k & 1];
+        a.out_pitch = last ? dst_pe : bpitch[k & 1];
+        a.err = err;
+        int grid;
+        decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, p->inv_warps_target, &a, &grid, 4);
+        mark(p, k, 0, st);
+        if (launch_inv_fused(elem_kind, sch, g.n, a, grid, st) != cudaSuccess) return DWT2D_ERR_CUDA;
+        mark(p, k, 1, st);
+        ll_in = a.out;
+        ll_pitch = a.out_pitch;
+    }
+    return DWT2D_OK;
+}
+
+// Steps of one level in forward order: (kind, coefficient).
+int step_list(const dwt2d_plan_s* p, int* kinds, float* coefs) {
+    const int sch = base_scheme(p->scheme);
+    int n = 0;
+    if (p->wavelet == DWT2D_CDF97) {
+        const float pu[2][2] = {{-1.586134342059924f, -0.052980118572961f},
+                                {0.882911075530934f, 0.443506852043971f}};
+        for (int k = 0; k < 2; ++k) {
+            if (sch == SCH_SEP) {
+                kinds[n] = P_TH; coefs[n++] = pu[k][0];
+                kinds[n] = P_TV; coefs[n++] = pu[k][0];
+                kinds[n] = P_SH; coefs[n++] = pu[k][1];
+                kinds[n] = P_SV; coefs[n++] = pu[k][1];
+            } else {
+                kinds[n] = sch == SCH_RED ? P_TR : P_T; coefs[n++] = pu[k][0];
+                kinds[n] = sch == SCH_RED ? P_SR : P_S; coefs[n++] = pu[k][1];
+            }
+        }
+    } else {
+        if (sch == SCH_SEP) {
+            kinds[n] = P_TH; coefs[n++] = 0.f;
+            kinds[n] = P_TV; coefs[n++] = 0.f;
+            kinds[n] = P_SH; coefs[n++] = 0.f;
+            kinds[n] = P_SV; coefs[n++] = 0.f;
+        } else {
+            kinds[n] = P_T; coefs[n++] = 0.f;
+            kinds[n] = P_S; coefs[n++] = 0.f;
+        }
+    }
+    return n;
+}
+
+dwt2d_status run_multipass(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t sp, void* dst,
+                           int64_t dp, void* ws, cudaStream_t st) {
+    const int elem_kind = p->dtype == DWT2D_I32 ? 1 : 0;
+    char* wsb = reinterpret_cast<char*>(ws);
+    void* X[2] = {wsb + p->off_x, wsb + p->off_y};
+    void* LLb[2] = {wsb + p->off_a, wsb + p->off_b};
+    const long long llp[2] = {p->pitch_a, p->pitch_b};
+    const long long src_pe = sp / p->elem, dst_pe = dp / p->elem;
+    int kinds[8];
+    float coefs[8];
+    const int nsteps = step_list(p, kinds, coefs);
+
+    auto interleaved = [](const void* ptr, long long pitch) {
+        Layout L;
+        L.p = ptr;
+        L.pitch = pitch;
+        L.ll = nullptr;
+        L.ll_pitch = 0;
+        L.kind = 0;
+        return L;
+    };
+    auto mallat = [](const void* ptr, long long pitch, const void* ll, long long llpitch) {
+        Layout L;
+        L.p = ptr;
+        L.pitch = pitch;
+        L.ll = ll;
+        L.ll_pitch = llpitch;
+        L.kind = 1;
+        return L;
+    };
+
+    if (fwd) {
+        Layout in = interleaved(src, src_pe);
+        for (int l = 0; l < p->levels; ++l) {
+            const int h = p->hs[l], w = p->ws[l];
+            const bool lastlev = l == p->levels - 1;
+            const void* llout = lastlev ? dst : LLb[l & 1];
+            const long long llout_p = lastlev ? dst_pe : llp[l & 1];
+            for (int k = 0; k < nsteps; ++k) {
+                PassArgs a;
+                memset(&a, 0, sizeof(a));
+                a.h = h;
+                a.w = w;
+                a.src = k == 0 ? in : interleaved(X[(k - 1) & 1], p->pitch_x);
+                const bool lastk = k == nsteps - 1;
+                a.dst = lastk ? mallat(dst, dst_pe, llout, llout_p) : interleaved(X[k & 1], p->pitch_x);
+                a.coef = coefs[k];
+                if (lastk && p->wavelet == DWT2D_CDF97) {
+                    level_scale(h, w, false, a.s);
+                    a.scale_out = 1;
+                }
+                mark(p, l * nsteps + k, 0, st);
+                if (launch_pass(elem_kind, kinds[k], true, a, st) != cudaSuccess) return DWT2D_ERR_CUDA;
+                mark(p, l * nsteps + k, 1, st);
+            }
+            in = interleaved(llout, llout_p);
+        }
+        return DWT2D_OK;
+    }
+    const void* llin = src;
+    long long llin_p = src_pe;
+    for (int l = p->levels - 1, j = 0; l >= 0; --l, ++j) {
+        const int h = p->hs[l], w = p->ws[l];
+        const bool lastlev = l == 0;
+        void* out = lastlev ? dst : LLb[j & 1];
+        const long long out_p = lastlev ? dst_pe : llp[j & 1];
+        for (int k = 0; k < nsteps; ++k) {
+            const int step = nsteps - 1 - k;  // undo in reverse order
+            PassArgs a;
+            memset(&a, 0, sizeof(a));
+            a.h = h;
+            a.w = w;
+            a.src = k == 0 ? mallat(src, src_pe, llin, llin_p) : interleaved(X[(k - 1) & 1], p->pitch_x);
+            a.dst = k == nsteps - 1 ? interleaved(out, out_p) : interleaved(X[k & 1], p->pitch_x);
+            a.coef = -coefs[step];
+            if (k == 0 && p->wavelet == DWT2D_CDF97) {
+                level_scale(h, w, true, a.s);
+                a.scale_in = 1;
+            }
+            mark(p, j * nsteps + k, 0, st);
+            if (launch_pass(elem_kind, kinds[step], false, a, st) != cudaSuccess) return DWT2D_ERR_CUDA;
+            mark(p, j * nsteps + k, 1, st);
+        }
+        llin = out;
+        llin_p = out_p;
+    }
+    return DWT2D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,
+                        dwt2d_wavelet wavelet, dwt2d_scheme scheme, dwt2d_boundary boundary,
+                        dwt2d_dtype dtype, size_t* workspace_bytes) {
+    if (!out || !workspace_bytes) return DWT2D_ERR_INVALID;
+    *out = nullptr;
+    if (height < 1 || width < 1 || height > 65536 || width > 65536) return DWT2D_ERR_INVALID;
+    if (levels < 1 || levels > 16) return DWT2D_ERR_INVALID;
+    if (boundary != DWT2D_SYMMETRIC_WHOLE) return DWT2D_ERR_UNSUPPORTED;
+    if (scheme < DWT2D_SEPARABLE || scheme > DWT2D_NONSEP_REDUCED_MULTIPASS) return DWT2D_ERR_INVALID;
+    if (!((wavelet == DWT2D_CDF97 && dtype == DWT2D_F32) ||
+          (wavelet == DWT2D_LEGALL53 && dtype == DWT2D_I32)))
+        return DWT2D_ERR_UNSUPPORTED;
+    dwt2d_plan_s* p = (dwt2d_plan_s*)calloc(1, sizeof(dwt2d_plan_s));
+    if (!p) return DWT2D_ERR_NOMEM;
+    p->H = height;
+    p->W = width;
+    p->levels = levels;
+    p->wavelet = wavelet;
+    p->scheme = scheme;
+    p->dtype = dtype;
+    p->elem = 4;
+    int h = height, w = width;
+    for (int l = 0; l < levels; ++l) {
+        p->hs[l] = h;
+        p->ws[l] = w;
+        h = (h + 1) / 2;
+        w = (w + 1) / 2;
+    }
+    // level groups: fuse up to DWT2D_FUSE (default 3) levels per launch
+    int maxf = env_int("DWT2D_FUSE", 3);
+    if (maxf < 1) maxf = 1;
+    if (maxf > kMaxFused) maxf = kMaxFused;
+    p->ngroups = 0;
+    for (int l = 0; l < levels;) {
+        const int n = levels - l < maxf ? levels - l : maxf;
+        p->groups[p->ngroups].first = l;
+        p->groups[p->ngroups].n = n;
+        ++p->ngroups;
+        l += n;
+    }
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    p->sm_count = sms;
+    p->fwd_warps_target = sms * env_int("DWT2D_FWD_WARPS_PER_SM", 12);
+    p->inv_warps_target = sms * env_int("DWT2D_INV_WARPS_PER_SM", 16);
+    p->min_segq = env_int("DWT2D_MIN_SEGQ", 8);
+
+    // workspace: header | LL buffer A | LL buffer B | (multipass) X | Y
+    size_t off = kHeader;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    long long pa = 1, pb = 1;
+    size_t ba = 0, bb = 0;
+    if (multipass(scheme)) {
+        // LLs alternate between A and B in both directions; size both for LL of level 1
+        if (levels > 1) {
+            const int lh = (p->hs[0] + 1) / 2, lw = (p->ws[0] + 1) / 2;
+            pa = pb = round_pitch(lw, p->elem);
+            ba = bb = (size_t)pa * lh * p->elem;
+        }
+    } else {
+        for (int gi = 0; gi + 1 < p->ngroups; ++gi) {
+            const Group g = p->groups[gi];
+            const int last = g.first + g.n - 1;
+            const int lh = (p->hs[last] + 1) / 2, lw = (p->ws[last] + 1) / 2;
+            const long long pp = round_pitch(lw, p->elem);
+            const size_t b = (size_t)pp * lh * p->elem;
+            // forward writes group gi's LL to buffer gi & 1; the inverse uses the
+            // same buffers for the LL it produces, which have the same sizes
+            if ((gi & 1) == 0) { if (b > ba) { ba = b; pa = pp; } }
+            else { if (b > bb) { bb = b; pb = pp; } }
+        }
+        // inverse order: launch k writes buffer k & 1; launch k produces the LL
+        // that group (ngroups - 2 - k) produced in the forward direction
+        for (int k = 0; k + 1 < p->ngroups; ++k) {
+            const Group g = p->groups[p->ngroups - 2 - k];
+            const int last = g.first + g.n - 1;
+            const int lh = (p->hs[last] + 1) / 2, lw = (p->ws[last] + 1) / 2;
+            const long long pp = round_pitch(lw, p->elem);
+            const size_t b = (size_t)pp * lh * p->elem;
+            if ((k & 1) == 0) { if (b > ba) { ba = b; pa = pp; } }
+            else { if (b > bb) { bb = b; pb = pp; } }
+        }
+    }
+    p->off_a = take(ba);
+    p->pitch_a = pa;
+    p->off_b = take(bb);
+    p->pitch_b = pb;
+    if (multipass(scheme)) {
+        const long long px = round_pitch(width + (width & 1), p->elem);
+        const size_t bx = (size_t)px * (height + (height & 1)) * p->elem;
+        p->off_x = take(bx);
+        p->off_y = take(bx);
+        p->pitch_x = px;
+    }
+    p->ws_bytes = off;
+    *workspace_bytes = off;
+    *out = p;
+    return DWT2D_OK;
+}
+
+dwt2d_status dwt2d_forward(dwt2d_plan_t p, const void* d_src, int64_t sp, void* d_dst, int64_t dp,
+                           void* d_ws, float scale, void* stream) {
+    (void)scale;
+    dwt2d_status s = check_buffers(p, d_src, sp, d_dst, dp, d_ws);
+    if (s != DWT2D_OK) return s;
+    if (d_src == d_dst) return DWT2D_ERR_INVALID;
+    return multipass(p->scheme) ? run_multipass(p, true, d_src, sp, d_dst, dp, d_ws, as_stream(stream))
+                                : run_fused(p, true, d_src, sp, d_dst, dp, d_ws, as_stream(stream));
+}
+
+dwt2d_status dwt2d_inverse(dwt2d_plan_t p, const void* d_src, int64_t sp, void* d_dst, int64_t dp,
+                           void* d_ws, float scale, void* stream) {
+    (void)scale;
+    dwt2d_status s = check_buffers(p, d_src, sp, d_dst, dp, d_ws);
+    if (s != DWT2D_OK) return s;
+    if (d_src == d_dst) return DWT2D_ERR_INVALID;
+    return multipass(p->scheme) ? run_multipass(p, false, d_src, sp, d_dst, dp, d_ws, as_stream(stream))
+                                : run_fused(p, false, d_src, sp, d_dst, dp, d_ws, as_stream(stream));
+}
+
+static dwt2d_status run_host(dwt2d_plan_t p, bool fwd, const void* h_src, int64_t hsp, void* h_dst,
+                             int64_t hdp, void* d_in, void* d_out, int64_t dpitch, void* d_ws,
+                             float scale, void* stream) {
+    if (!p || !h_src || !h_dst) return DWT2D_ERR_INVALID;
+    const int64_t row = (int64_t)p->W * p->elem;
+    if (hsp < row || hdp < row) return DWT2D_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    if (cudaMemcpy2DAsync(d_in, dpitch, h_src, hsp, row, p->H, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return DWT2D_ERR_CUDA;
+    dwt2d_status s = fwd ? dwt2d_forward(p, d_in, dpitch, d_out, dpitch, d_ws, scale, stream)
+                         : dwt2d_inverse(p, d_in, dpitch, d_out, dpitch, d_ws, scale, stream);
+    if (s != DWT2D_OK) return s;
+    if (cudaMemcpy2DAsync(h_dst, hdp, d_out, dpitch, row, p->H, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return DWT2D_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? DWT2D_OK : DWT2D_ERR_CUDA;
+}
+
+dwt2d_status dwt2d_forward_host(dwt2d_plan_t p, const void* h_src, int64_t hsp, void* h_dst,
+                                int64_t hdp, void* d_in, void* d_out, int64_t dpitch, void* d_ws,
+                                float scale, void* stream) {
+    return run_host(p, true, h_src, hsp, h_dst, hdp, d_in, d_out, dpitch, d_ws, scale, stream);
+}
+
+dwt2d_status dwt2d_inverse_host(dwt2d_plan_t p, const void* h_src, int64_t hsp, void* h_dst,
+                                int64_t hdp, void* d_in, void* d_out, int64_t dpitch, void* d_ws,
+                                float scale, void* stream) {
+    return run_host(p, false, h_src, hsp, h_dst, hdp, d_in, d_out, dpitch, d_ws, scale, stream);
+}
+
+dwt2d_status dwt2d_workspace_init(void* d_ws, void* stream) {
+    if (!d_ws) return DWT2D_ERR_INVALID;
+    if (!aligned16(d_ws)) return DWT2D_ERR_ALIGN;
+    return cudaMemsetAsync(d_ws, 0, sizeof(int), as_stream(stream)) == cudaSuccess ? DWT2D_OK
+                                                                                   : DWT2D_ERR_CUDA;
+}
+
+dwt2d_status dwt2d_workspace_status(void* d_ws, void* stream) {
+    if (!d_ws) return DWT2D_ERR_INVALID;
+    int h = 0;
+    cudaStream_t st = as_stream(stream);
+    if (cudaMemcpyAsync(&h, d_ws, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return DWT2D_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return DWT2D_ERR_CUDA;
+    if (h != 0) {
+        if (cudaMemsetAsync(d_ws, 0, sizeof(int), st) != cudaSuccess) return DWT2D_ERR_CUDA;
+        return (dwt2d_status)h;
+    }
+    return DWT2D_OK;
+}
+
+dwt2d_status dwt2d_plan_info(dwt2d_plan_t p, int32_t* launches, int32_t* fused, int32_t* n_groups) {
+    if (!p) return DWT2D_ERR_INVALID;
+    if (multipass(p->scheme)) {
+        int kinds[8];
+        float coefs[8];
+        const int n = step_list(p, kinds, coefs);
+        if (launches) *launches = n * p->levels;
+        if (n_groups) *n_groups = p->levels;
+        if (fused)
+            for (int l = 0; l < p->levels; ++l) fused[l] = 1;
+        return DWT2D_OK;
+    }
+    if (launches) *launches = p->ngroups;
+    if (n_groups) *n_groups = p->ngroups;
+    if (fused)
+        for (int g = 0; g < p->ngroups; ++g) fused[g] = p->groups[g].n;
+    return DWT2D_OK;
+}
+
+dwt2d_status dwt2d_plan_set_launch_events(dwt2d_plan_t p, void** events, int32_t count) {
+    if (!p || count < 0) return DWT2D_ERR_INVALID;
+    p->events = events ? reinterpret_cast<cudaEvent_t*>(events) : nullptr;
+    p->nevents = events ? count : 0;
+    return DWT2D_OK;
+}
+
+void dwt2d_plan_destroy(dwt2d_plan_t p) { free(p); }
+
+const char* dwt2d_status_string(dwt2d_status s) {
+    switch (s) {
+        case DWT2D_OK: return "ok";
+        case DWT2D_ERR_INVALID: return "invalid argument";
+        case DWT2D_ERR_UNSUPPORTED: return "unsupported wavelet/dtype/scheme";
+        case DWT2D_ERR_ALIGN: return "pointer or pitch not 16-byte aligned";
+        case DWT2D_ERR_NOMEM: return "host allocation failed";
+        case DWT2D_ERR_CUDA: return "CUDA error";
+        case DWT2D_ERR_TIMEOUT: return "kernel wait timed out";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

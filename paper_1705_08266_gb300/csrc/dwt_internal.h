@@ -1,0 +1,76 @@
+// Host/device argument blocks shared by the C ABI and the kernel files.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dwt {
+
+constexpr int kMaxFused = 3;  // levels fused in one streaming launch
+
+// Lifting schemes: separable (Sec. 2), non-separable and its reduced form (Sec. 3).
+enum Scheme { SCH_SEP = 0, SCH_NONSEP = 1, SCH_RED = 2 };
+
+// Geometry of one warp-streaming launch (forward or inverse, 1..3 levels).
+struct LevelArgs {
+    int h, w;     // extent this level transforms (image or LL of the level before)
+    float s[4];   // forward: scale of LL, HL, LH, HH; inverse: its reciprocal
+};
+
+struct FusedArgs {
+    LevelArgs lv[kMaxFused];
+    // Mallat coefficient array (forward: written; inverse: read), element pitch
+    void* mallat;
+    long long mallat_pitch;
+    // forward: LL of the last fused level is written here;
+    // inverse: LL of the coarsest fused level is read from here
+    void* ll;
+    long long ll_pitch;
+    // inverse only: the reconstructed image (or LL of the finest fused level - 1)
+    void* out;
+    long long out_pitch;
+    int nstrips, nsegs, segq;        // warp work items = nstrips * nsegs
+    int valid_px, xoff;              // strip width in input pixels and left halo offset
+    int lane_lo, lane_hi;            // lanes that store
+    int* err;                        // device status word (0 = ok)
+};
+
+// Where a multipass kernel reads or writes a level's coefficients.
+struct Layout {
+    const void* p;       // kind 0: interleaved image layout; kind 1: Mallat array (details)
+    long long pitch;     // elements
+    const void* ll;      // kind 1: the LL band (may be inside p)
+    long long ll_pitch;  // elements
+    int kind;
+};
+
+// One pass of the multipass (off-chip exchange) scheme.
+struct PassArgs {
+    int h, w;          // extent of the level
+    Layout src, dst;
+    float s[4];        // per-component scale applied on load (scale_in) or store (scale_out)
+    float coef;        // float lifting coefficient of this step, sign included
+    int scale_in, scale_out;
+};
+
+// Kernel-geometry constants of the streaming forward kernel.
+constexpr int kFwdWarps = 4;        // warps per CTA (each warp is independent)
+constexpr int kFwdSlots = 4;        // TMA ring depth per warp
+constexpr int kFwdSlotRows = 4;     // image rows per TMA box
+constexpr int kBoxW = 256;          // pixels per box row = 32 lanes x 8 pixels
+constexpr int kLanePx = 8;          // pixels per lane at level 1 (4 quadruple columns)
+
+size_t fwd_smem_bytes(int elem_bytes);
+
+cudaError_t launch_fwd_fused(int elem, int scheme, int nl, const CUtensorMap& map,
+                             const FusedArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_inv_fused(int elem, int scheme, int nl, const FusedArgs& a, int grid,
+                             cudaStream_t st);
+
+// elem: 0 = float32, 1 = int32.  kind: the step (see dwt_multipass.cu).
+cudaError_t launch_pass(int elem, int kind, bool fwd, const PassArgs& a, cudaStream_t st);
+
+enum PassKind { P_TH = 0, P_TV, P_SH, P_SV, P_T, P_S, P_TR, P_SR };
+
+}  // namespace dwt

@@ -1,0 +1,127 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several warp strips (240 / 224 / 192 pixels) and several row
+segments with ragged tails, odd sizes, axes of length 1 and 2.  CDF 9/7
+float32 must stay within 1e-5 * max|x| per level; reversible 5/3 int32 must be
+bit-exact for every scheme.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import lifting as L
+from paper_1705_08266_gb300 import dwt2d as D
+from tests.parity_util import (assert_forward_matches, assert_inverse_matches, device_image, host,
+                               make_input)
+
+pytestmark = pytest.mark.gpu
+
+SCHEMES = list(D.SCHEMES)
+SHAPES_LEVELS = [
+    ((8, 8), 1), ((8, 8), 3), ((7, 9), 2), ((9, 7), 3), ((1, 9), 2), ((9, 1), 2), ((1, 1), 2),
+    ((2, 2), 1), ((3, 3), 2), ((33, 70), 3), ((64, 300), 4), ((130, 257), 5), ((40, 513), 3),
+    ((512, 512), 1), ((512, 512), 5), ((65, 1000), 6), ((301, 497), 4),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    D.lib()
+
+
+def _fwd_inv(x, levels, wavelet, scheme):
+    h, w = x.shape
+    plan = D.Plan(h, w, levels, wavelet, scheme)
+    ws = plan.workspace()
+    xd = device_image(x)
+    c = plan.forward(xd, workspace=ws)
+    ref = L.forward(x, levels, wavelet)
+    cref = device_image(ref.astype(x.dtype))
+    y = plan.inverse(cref, workspace=ws)
+    torch.cuda.synchronize()
+    assert plan.status(ws) == 0
+    return host(c), host(y), ref
+
+
+@pytest.mark.parametrize("wavelet", ["cdf97", "legall53"])
+@pytest.mark.parametrize("shape,levels", SHAPES_LEVELS)
+def test_parity_all_schemes(wavelet, shape, levels):
+    x = make_input(wavelet, *shape, seed=1705 + shape[0] * 7 + shape[1])
+    for scheme in SCHEMES:
+        c, y, ref = _fwd_inv(x, levels, wavelet, scheme)
+        tag = f"{wavelet} {scheme} {shape} L{levels}"
+        assert_forward_matches(c, x, levels, wavelet, tag)
+        assert_inverse_matches(y, ref.astype(x.dtype), levels, wavelet, x, tag)
+
+
+@pytest.mark.parametrize("fuse", ["1", "2", "3"])
+@pytest.mark.parametrize("wavelet", ["cdf97", "legall53"])
+def test_parity_many_segments_and_fusion(monkeypatch, fuse, wavelet):
+    """Tiny row segments (many warps per strip) and every fusion depth."""
+    monkeypatch.setenv("DWT2D_FUSE", fuse)
+    monkeypatch.setenv("DWT2D_MIN_SEGQ", "1")
+    monkeypatch.setenv("DWT2D_FWD_WARPS_PER_SM", "4000")
+    monkeypatch.setenv("DWT2D_INV_WARPS_PER_SM", "4000")
+    for shape, levels in [((200, 777), 3), ((97, 515), 5), ((450, 250), 4)]:
+        x = make_input(wavelet, *shape, seed=11 + shape[1])
+        for scheme in ("separable", "nonsep", "nonsep_reduced"):
+            c, y, ref = _fwd_inv(x, levels, wavelet, scheme)
+            tag = f"fuse={fuse} {wavelet} {scheme} {shape} L{levels}"
+            assert_forward_matches(c, x, levels, wavelet, tag)
+            assert_inverse_matches(y, ref.astype(x.dtype), levels, wavelet, x, tag)
+
+
+@pytest.mark.parametrize("wavelet", ["cdf97", "legall53"])
+@pytest.mark.parametrize("shape", [(16, 65536), (65536, 16)])
+def test_extreme_aspect(wavelet, shape):
+    """Largest allowed side (65536) with a short other side, 6 levels."""
+    x = make_input(wavelet, *shape, seed=3)
+    c, y, ref = _fwd_inv(x, 6, wavelet, "nonsep_reduced")
+    assert_forward_matches(c, x, 6, wavelet, f"{shape}")
+    assert_inverse_matches(y, ref.astype(x.dtype), 6, wavelet, x, f"{shape}")
+
+
+@pytest.mark.parametrize("wavelet", ["cdf97", "legall53"])
+def test_constant_and_ramp(wavelet):
+    """Constant image: zero details and LL = value; ramp: zero interior details."""
+    dt = np.int32 if wavelet == "legall53" else np.float32
+    for x in (np.full((130, 257), 100, dtype=dt),
+              (3 * np.arange(257)[None, :] + 5 * np.arange(130)[:, None]).astype(dt)):
+        for scheme in SCHEMES:
+            c, _, _ = _fwd_inv(x, 3, wavelet, scheme)
+            assert_forward_matches(c, x, 3, wavelet, scheme)
+
+
+def test_round_trip_gpu_only():
+    """inverse(forward(x)) == x through the GPU alone (5/3 exactly)."""
+    for wavelet in ("cdf97", "legall53"):
+        x = make_input(wavelet, 777, 1029, seed=5)
+        for scheme in SCHEMES:
+            plan = D.Plan(777, 1029, 5, wavelet, scheme)
+            ws = plan.workspace()
+            y = host(plan.inverse(plan.forward(device_image(x), workspace=ws), workspace=ws))
+            if wavelet == "legall53":
+                assert np.array_equal(y, x), scheme
+            else:
+                # forward and inverse each stay within TOL per level: 2 * levels * TOL overall
+                assert np.max(np.abs(y - x)) <= 2 * 5 * 1e-5 * np.max(np.abs(x)), scheme
+
+
+def test_host_entry_points():
+    """dwt2d_forward_host / inverse_host: host buffers in, host buffers out."""
+    x = make_input("cdf97", 300, 500, seed=8)
+    plan = D.Plan(300, 500, 4, "cdf97", "nonsep_reduced")
+    ws = plan.workspace()
+    hs = torch.from_numpy(x).pin_memory()
+    hd = torch.empty_like(hs).pin_memory()
+    din = D.empty_image(300, 500)
+    dout = D.empty_image(300, 500)
+    plan.forward_host(hs, hd, din, dout, ws)
+    assert_forward_matches(hd.numpy(), x, 4, "cdf97", "host fwd")
+    back = torch.empty_like(hs).pin_memory()
+    plan.inverse_host(hd, back, din, dout, ws)
+    assert np.max(np.abs(back.numpy() - x)) <= 1e-5 * np.max(np.abs(x))
