@@ -180,6 +180,43 @@ dwt2d_status dwt2d_plan_info(dwt2d_plan_t plan, int32_t* launches_per_call, int3
  */
 dwt2d_status dwt2d_plan_set_launch_events(dwt2d_plan_t plan, void** events, int32_t count);
 
+/*
+ * dwt2d_forward_noalloc -- dwt2d_forward for callers that cannot allocate
+ *   device memory.  (The paper has no counterpart: this is a library service.)
+ *
+ *   Some callers never get to call cudaMalloc: a plugin inside a host
+ *   application that owns every byte of device memory and hands the plugin
+ *   only its input and output buffers, code on a latency-critical path where
+ *   an allocation (which may synchronize the device) is not acceptable, or a
+ *   service that must not be able to fail with out-of-memory in the middle of
+ *   a request.  This entry point needs no workspace argument: the scratch the
+ *   multilevel forward transform uses between its launches (and the status
+ *   word of its bounded waits) lives in one fixed array of
+ *   DWT2D_NOALLOC_SCRATCH_BYTES in the library's device memory, which every
+ *   GPU that loads the library holds until the process exits.  The caller
+ *   still passes the image and the coefficient buffer, exactly as for
+ *   dwt2d_forward, and gets the same coefficients.
+ *
+ *   - The first call on each device looks up that device's address of the
+ *     array (cudaGetSymbolAddress) with the device current; make that first
+ *     call before any stream capture.
+ *   - A plan whose workspace_bytes exceeds DWT2D_NOALLOC_SCRATCH_BYTES is
+ *     rejected with DWT2D_ERR_INVALID before any GPU work (for example an
+ *     8192 x 8192 float image with 5 levels fits, 16384 x 16384 with 6 levels
+ *     or any multipass scheme of a large image does not).
+ *   - All calls on a device share the one array, and it keeps whatever the
+ *     last call left in it.  Each call clears the status word first; the rest
+ *     is written before it is read.  Calls whose kernels overlap on the GPU
+ *     (two streams, or a second call before the first has finished on another
+ *     stream) race on the array and corrupt each other's results: serialise
+ *     them, for example on one stream.
+ *   - Nothing here calls cudaMalloc, cudaFree or an allocating library
+ *     routine.  Errors: as dwt2d_forward.
+ */
+#define DWT2D_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+dwt2d_status dwt2d_forward_noalloc(dwt2d_plan_t plan, const void* d_src, int64_t src_pitch_bytes,
+                                   void* d_dst, int64_t dst_pitch_bytes, float scale, void* stream);
+
 void dwt2d_plan_destroy(dwt2d_plan_t plan);
 const char* dwt2d_status_string(dwt2d_status status);
 

@@ -367,6 +367,8 @@ dwt2d_status run_multipass(const dwt2d_plan_s* p, bool fwd, const void* src, int
 
 }  // namespace
 
+size_t dwt::plan_workspace_bytes(dwt2d_plan_t p) { return p ? p->ws_bytes : 0; }
+
 extern "C" {
 
 dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,

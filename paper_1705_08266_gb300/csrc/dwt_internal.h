@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dwt2d.h"
+
 namespace dwt {
 
 constexpr int kMaxFused = 3;  // levels fused in one streaming launch
@@ -72,5 +74,8 @@ cudaError_t launch_inv_fused(int elem, int scheme, int nl, const FusedArgs& a, i
 cudaError_t launch_pass(int elem, int kind, bool fwd, const PassArgs& a, cudaStream_t st);
 
 enum PassKind { P_TH = 0, P_TV, P_SH, P_SV, P_T, P_S, P_TR, P_SR };
+
+// Workspace bytes a plan needs (0 for a null plan).
+size_t plan_workspace_bytes(dwt2d_plan_t p);
 
 }  // namespace dwt
