@@ -310,7 +310,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
                 "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": f"fwd_fused_kernel<float, nonsep_reduced, {fused[0]}> (launch {dom})",
+                "kernel": f"fwd_fused_kernel<float, nonsep_reduced, {fused[0]} levels> (launch {dom})",
                 "kernel_ms": round(launch_ms[dom], 5),
                 "alg_bytes_per_launch": alg_bytes_dom,
                 "whole_step": {"strict_bytes": strict_bytes,

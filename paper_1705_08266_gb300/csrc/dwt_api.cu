@@ -33,6 +33,7 @@ struct dwt2d_plan_s {
     int ngroups;
     int sm_count;
     int fwd_warps_target, inv_warps_target;
+    int fwd_q1;  // quadruple columns per lane of the forward kernel (2 or 4)
     int min_segq;
     // workspace layout (bytes from the start of the workspace)
     size_t off_a, off_b, off_x, off_y;
@@ -77,15 +78,15 @@ void level_scale(int h, int w, bool inverse, float s[4]) {
 
 // Lanes whose every column at the deepest fused level is valid, for a warp of
 // 32 lanes x 4 level-1 quadruple columns and a lifting radius rho (quadruples).
-void valid_lanes(int nl, int rho, int* lo_out, int* hi_out) {
-    int lo = rho, hi = 128 - rho;  // level-1 valid quadruple columns [lo, hi)
+void valid_lanes(int nl, int rho, int q1, int* lo_out, int* hi_out) {
+    int lo = rho, hi = 32 * q1 - rho;  // level-1 valid quadruple columns [lo, hi)
     for (int l = 2; l <= nl; ++l) {
         const int nlo = (lo + 2 * rho + 1) / 2;          // ceil((lo + 2 rho) / 2)
         const int nhi = (hi - 2 - 2 * rho) / 2 + 1;      // floor((hi - 2 - 2 rho) / 2) + 1
         lo = nlo;
         hi = nhi;
     }
-    const int q = 4 >> (nl - 1);
+    const int q = q1 >> (nl - 1);
     int llo = 32, lhi = 0;
     for (int l = 0; l < 32; ++l) {
         if (l * q >= lo && l * q + q <= hi) {
@@ -117,12 +118,12 @@ EncodeTiledFn encode_fn() {
 }
 
 dwt2d_status make_map(CUtensorMap* map, const void* base, int h, int w, long long pitch_elems,
-                      int elem, bool is_int) {
+                      int elem, bool is_int, int box_w) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return DWT2D_ERR_CUDA;
     const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
     const cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * elem)};
-    const cuuint32_t box[2] = {(cuuint32_t)kBoxW, (cuuint32_t)kFwdSlotRows};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)kFwdSlotRows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = fn(map, is_int ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                           2, const_cast<void*>(base), dims, strides, box, estr,
@@ -144,10 +145,10 @@ dwt2d_status check_buffers(const dwt2d_plan_s* p, const void* src, int64_t sp, c
 }
 
 // Warp work decomposition of one streaming launch.
-void decompose(const dwt2d_plan_s* p, int w_first, int rows, int nl, int rho, int target_warps,
-               FusedArgs* a, int* grid, int warps_per_block) {
-    valid_lanes(nl, rho, &a->lane_lo, &a->lane_hi);
-    const int qn = 4 >> (nl - 1);
+void decompose(const dwt2d_plan_s* p, int w_first, int rows, int nl, int rho, int q1,
+               int target_warps, FusedArgs* a, int* grid, int warps_per_block) {
+    valid_lanes(nl, rho, q1, &a->lane_lo, &a->lane_hi);
+    const int qn = q1 >> (nl - 1);
     a->valid_px = (a->lane_hi - a->lane_lo) * qn * (1 << nl);
     a->xoff = a->lane_lo * qn * (1 << nl);
     a->nstrips = (w_first + a->valid_px - 1) / a->valid_px;
@@ -198,14 +199,17 @@ dwt2d_status run_fused(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t
             a.ll = last ? dst : bufs[gi & 1];
             a.ll_pitch = last ? dst_pe : bpitch[gi & 1];
             a.err = err;
+            const int q1 = g.n >= 3 ? 4 : p->fwd_q1;
             CUtensorMap map;
-            dwt2d_status s = make_map(&map, in, a.lv[0].h, a.lv[0].w, in_pitch, p->elem, elem_kind == 1);
+            dwt2d_status s = make_map(&map, in, a.lv[0].h, a.lv[0].w, in_pitch, p->elem, elem_kind == 1,
+                                      64 * q1);
             if (s != DWT2D_OK) return s;
             const int hN = a.lv[g.n - 1].h;
             int grid;
-            decompose(p, a.lv[0].w, (hN + 1) / 2, g.n, rho, p->fwd_warps_target, &a, &grid, kFwdWarps);
+            decompose(p, a.lv[0].w, (hN + 1) / 2, g.n, rho, q1, p->fwd_warps_target, &a, &grid,
+                      kFwdWarps);
             mark(p, gi, 0, st);
-            if (launch_fwd_fused(elem_kind, sch, g.n, map, a, grid, st) != cudaSuccess)
+            if (launch_fwd_fused(elem_kind, sch, g.n, q1, map, a, grid, st) != cudaSuccess)
                 return DWT2D_ERR_CUDA;
             mark(p, gi, 1, st);
             in = a.ll;
@@ -234,7 +238,7 @@ dwt2d_status run_fused(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t
         a.out_pitch = last ? dst_pe : bpitch[k & 1];
         a.err = err;
         int grid;
-        decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, p->inv_warps_target, &a, &grid, 4);
+        decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, 4, p->inv_warps_target, &a, &grid, 4);
         mark(p, k, 0, st);
         if (launch_inv_fused(elem_kind, sch, g.n, a, grid, st) != cudaSuccess) return DWT2D_ERR_CUDA;
         mark(p, k, 1, st);
@@ -399,13 +403,18 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
         h = (h + 1) / 2;
         w = (w + 1) / 2;
     }
-    // level groups: fuse up to DWT2D_FUSE (default 3) levels per launch
+    // level groups: the first launch fuses DWT2D_FUSE_FIRST levels (default 2),
+    // later launches up to DWT2D_FUSE (default 3) each
     int maxf = env_int("DWT2D_FUSE", 3);
     if (maxf < 1) maxf = 1;
     if (maxf > kMaxFused) maxf = kMaxFused;
+    int first = env_int("DWT2D_FUSE_FIRST", maxf < 2 ? maxf : 2);
+    if (first < 1) first = 1;
+    if (first > maxf) first = maxf;
     p->ngroups = 0;
     for (int l = 0; l < levels;) {
-        const int n = levels - l < maxf ? levels - l : maxf;
+        const int cap = p->ngroups == 0 ? first : maxf;
+        const int n = levels - l < cap ? levels - l : cap;
         p->groups[p->ngroups].first = l;
         p->groups[p->ngroups].n = n;
         ++p->ngroups;
@@ -416,9 +425,10 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
     p->sm_count = sms;
-    p->fwd_warps_target = sms * env_int("DWT2D_FWD_WARPS_PER_SM", 12);
+    p->fwd_warps_target = sms * env_int("DWT2D_FWD_WARPS_PER_SM", 16);
     p->inv_warps_target = sms * env_int("DWT2D_INV_WARPS_PER_SM", 16);
-    p->min_segq = env_int("DWT2D_MIN_SEGQ", 8);
+    p->min_segq = env_int("DWT2D_MIN_SEGQ", 2);
+    p->fwd_q1 = env_int("DWT2D_FWD_Q", 2) == 4 ? 4 : 2;
 
     // workspace: header | LL buffer A | LL buffer B | (multipass) X | Y
     size_t off = kHeader;

@@ -80,24 +80,26 @@ __device__ __forceinline__ T shfl_up(T v) {
     return __shfl_up_sync(kFull, v, 1);
 }
 
-// R[j] = v at column j+1, mirrored at the right border.
-template <class T, int Q>
+// R[j] = v at column j+1, mirrored at the right border (EDGE) or not (interior).
+template <bool EDGE, class T, int Q>
 __device__ __forceinline__ void right_nb(const T (&v)[Q], T (&R)[Q], unsigned m) {
     const T n = shfl_dn(v[0]);
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const T nb = (j + 1 < Q) ? v[j + 1] : n;
-        R[j] = ((m >> j) & 1u) ? nb : v[j];
+        if (EDGE) R[j] = ((m >> j) & 1u) ? nb : v[j];
+        else R[j] = nb;
     }
 }
-// L[j] = v at column j-1, mirrored at the left border.
-template <class T, int Q>
+// L[j] = v at column j-1, mirrored at the left border (EDGE) or not (interior).
+template <bool EDGE, class T, int Q>
 __device__ __forceinline__ void left_nb(const T (&v)[Q], T (&L)[Q], unsigned m) {
     const T p = shfl_up(v[Q - 1]);
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const T nb = (j > 0) ? v[j - 1] : p;
-        L[j] = ((m >> j) & 1u) ? nb : v[j];
+        if (EDGE) L[j] = ((m >> j) & 1u) ? nb : v[j];
+        else L[j] = nb;
     }
 }
 // Columns without odd samples take the odd sample of the column before.
@@ -121,9 +123,10 @@ enum Kind { K_NONE = 0, K_DOWN = 1, K_UP = 2 };
 
 // ------------------------------------------------------------------ ops ----
 // Every op names its vertical dependency (kind) and whether it needs the own
-// odd samples mirrored horizontally before it runs (kHsub).
+// odd samples mirrored horizontally before it runs (kHsub).  EDGE = false is
+// the interior form: no border substitution and both axes active, so the
+// coefficients are compile-time constants.
 
-// float, separable
 template <int ID, int SIGN>
 struct Coef;
 template <int SIGN>
@@ -135,15 +138,25 @@ struct Coef<2, SIGN> { static constexpr float v = SIGN * kGamma; };
 template <int SIGN>
 struct Coef<3, SIGN> { static constexpr float v = SIGN * kDelta; };
 
+template <bool EDGE>
+__device__ __forceinline__ float hcoef(float c, const LevelCtx& x) { return EDGE ? c * x.hf : c; }
+template <bool EDGE>
+__device__ __forceinline__ float vcoef(float c, const LevelCtx& x) { return EDGE ? c * x.vf : c; }
+template <bool EDGE>
+__device__ __forceinline__ bool hact(const LevelCtx& x) { return EDGE ? x.ha : true; }
+template <bool EDGE>
+__device__ __forceinline__ bool vact(const LevelCtx& x) { return EDGE ? x.va : true; }
+
+// float, separable (Sec. 2 matrices)
 template <int ID, int SIGN>
 struct OpFTH {
     static constexpr int kind = K_NONE;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<float, Q>& a, const LevelCtx& x) {
         float c0r[Q], c2r[Q];
-        right_nb(a.c[0], c0r, x.right);
-        right_nb(a.c[2], c2r, x.right);
-        const float p = Coef<ID, SIGN>::v * x.hf;
+        right_nb<EDGE>(a.c[0], c0r, x.right);
+        right_nb<EDGE>(a.c[2], c2r, x.right);
+        const float p = hcoef<EDGE>(Coef<ID, SIGN>::v, x);
 #pragma unroll
         for (int j = 0; j < Q; ++j) f_TH(a.c[1][j], a.c[3][j], a.c[0][j], c0r[j], a.c[2][j], c2r[j], p);
     }
@@ -151,10 +164,10 @@ struct OpFTH {
 template <int ID, int SIGN>
 struct OpFTV {
     static constexpr int kind = K_DOWN;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<float, Q>& a, const float (&n0)[Q],
                                                  const float (&n1)[Q], const LevelCtx& x) {
-        const float p = Coef<ID, SIGN>::v * x.vf;
+        const float p = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
 #pragma unroll
         for (int j = 0; j < Q; ++j) f_TV(a.c[2][j], a.c[3][j], a.c[0][j], n0[j], a.c[1][j], n1[j], p);
     }
@@ -162,16 +175,16 @@ struct OpFTV {
 template <int ID, int SIGN>
 struct OpFSH {
     static constexpr int kind = K_NONE;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<float, Q>& a, const LevelCtx& x) {
-        if (x.need_hsub) {
+        if (EDGE && x.need_hsub) {
             subst_odd(a.c[1], x.odd);
             subst_odd(a.c[3], x.odd);
         }
         float c1l[Q], c3l[Q];
-        left_nb(a.c[1], c1l, x.left);
-        left_nb(a.c[3], c3l, x.left);
-        const float u = Coef<ID, SIGN>::v * x.hf;
+        left_nb<EDGE>(a.c[1], c1l, x.left);
+        left_nb<EDGE>(a.c[3], c3l, x.left);
+        const float u = hcoef<EDGE>(Coef<ID, SIGN>::v, x);
 #pragma unroll
         for (int j = 0; j < Q; ++j) f_SH(a.c[0][j], a.c[2][j], a.c[1][j], c1l[j], a.c[3][j], c3l[j], u);
     }
@@ -180,27 +193,27 @@ template <int ID, int SIGN>
 struct OpFSV {
     static constexpr int kind = K_UP;
     static constexpr bool kHsub = false;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<float, Q>& a, const float (&up2)[Q],
                                                  const float (&up3)[Q], const LevelCtx& x) {
-        const float u = Coef<ID, SIGN>::v * x.vf;
+        const float u = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
 #pragma unroll
         for (int j = 0; j < Q; ++j) f_SV(a.c[0][j], a.c[1][j], a.c[2][j], up2[j], a.c[3][j], up3[j], u);
     }
 };
 
-// float, non-separable (RED = reduced form)
+// float, non-separable (Sec. 3; RED = reduced form)
 template <int ID, int SIGN, bool RED>
 struct OpFT {
     static constexpr int kind = K_DOWN;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<float, Q>& a, const float (&n0)[Q],
                                                  const float (&n1)[Q], const LevelCtx& x) {
         float c0r[Q], c2r[Q], n0r[Q];
-        right_nb(a.c[0], c0r, x.right);
-        right_nb(a.c[2], c2r, x.right);
-        right_nb(n0, n0r, x.right);
-        const float ph = Coef<ID, SIGN>::v * x.hf, pv = Coef<ID, SIGN>::v * x.vf;
+        right_nb<EDGE>(a.c[0], c0r, x.right);
+        right_nb<EDGE>(a.c[2], c2r, x.right);
+        right_nb<EDGE>(n0, n0r, x.right);
+        const float ph = hcoef<EDGE>(Coef<ID, SIGN>::v, x), pv = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             if (RED)
@@ -216,14 +229,14 @@ template <int ID, int SIGN, bool RED>
 struct OpFS {
     static constexpr int kind = K_UP;
     static constexpr bool kHsub = true;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<float, Q>& a, const float (&up2)[Q],
                                                  const float (&up3)[Q], const LevelCtx& x) {
         float c1l[Q], c3l[Q], u3l[Q];
-        left_nb(a.c[1], c1l, x.left);
-        left_nb(a.c[3], c3l, x.left);
-        left_nb(up3, u3l, x.left);
-        const float uh = Coef<ID, SIGN>::v * x.hf, uv = Coef<ID, SIGN>::v * x.vf;
+        left_nb<EDGE>(a.c[1], c1l, x.left);
+        left_nb<EDGE>(a.c[3], c3l, x.left);
+        left_nb<EDGE>(up3, u3l, x.left);
+        const float uh = hcoef<EDGE>(Coef<ID, SIGN>::v, x), uv = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             if (RED)
@@ -240,50 +253,54 @@ struct OpFS {
 template <int SIGN>
 struct OpITH {
     static constexpr int kind = K_NONE;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<int, Q>& a, const LevelCtx& x) {
         int c0r[Q], c2r[Q];
-        right_nb(a.c[0], c0r, x.right);
-        right_nb(a.c[2], c2r, x.right);
+        right_nb<EDGE>(a.c[0], c0r, x.right);
+        right_nb<EDGE>(a.c[2], c2r, x.right);
 #pragma unroll
-        for (int j = 0; j < Q; ++j) i_TH(a.c[1][j], a.c[3][j], a.c[0][j], c0r[j], a.c[2][j], c2r[j], x.ha, SIGN);
+        for (int j = 0; j < Q; ++j)
+            i_TH(a.c[1][j], a.c[3][j], a.c[0][j], c0r[j], a.c[2][j], c2r[j], hact<EDGE>(x), SIGN);
     }
 };
 template <int SIGN>
 struct OpITV {
     static constexpr int kind = K_DOWN;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<int, Q>& a, const int (&n0)[Q],
                                                  const int (&n1)[Q], const LevelCtx& x) {
 #pragma unroll
-        for (int j = 0; j < Q; ++j) i_TV(a.c[2][j], a.c[3][j], a.c[0][j], n0[j], a.c[1][j], n1[j], x.va, SIGN);
+        for (int j = 0; j < Q; ++j)
+            i_TV(a.c[2][j], a.c[3][j], a.c[0][j], n0[j], a.c[1][j], n1[j], vact<EDGE>(x), SIGN);
     }
 };
 template <int SIGN>
 struct OpISH {
     static constexpr int kind = K_NONE;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<int, Q>& a, const LevelCtx& x) {
-        if (x.need_hsub) {
+        if (EDGE && x.need_hsub) {
             subst_odd(a.c[1], x.odd);
             subst_odd(a.c[3], x.odd);
         }
         int c1l[Q], c3l[Q];
-        left_nb(a.c[1], c1l, x.left);
-        left_nb(a.c[3], c3l, x.left);
+        left_nb<EDGE>(a.c[1], c1l, x.left);
+        left_nb<EDGE>(a.c[3], c3l, x.left);
 #pragma unroll
-        for (int j = 0; j < Q; ++j) i_SH(a.c[0][j], a.c[2][j], a.c[1][j], c1l[j], a.c[3][j], c3l[j], x.ha, SIGN);
+        for (int j = 0; j < Q; ++j)
+            i_SH(a.c[0][j], a.c[2][j], a.c[1][j], c1l[j], a.c[3][j], c3l[j], hact<EDGE>(x), SIGN);
     }
 };
 template <int SIGN>
 struct OpISV {
     static constexpr int kind = K_UP;
     static constexpr bool kHsub = false;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<int, Q>& a, const int (&up2)[Q],
                                                  const int (&up3)[Q], const LevelCtx& x) {
 #pragma unroll
-        for (int j = 0; j < Q; ++j) i_SV(a.c[0][j], a.c[1][j], a.c[2][j], up2[j], a.c[3][j], up3[j], x.va, SIGN);
+        for (int j = 0; j < Q; ++j)
+            i_SV(a.c[0][j], a.c[1][j], a.c[2][j], up2[j], a.c[3][j], up3[j], vact<EDGE>(x), SIGN);
     }
 };
 
@@ -291,21 +308,21 @@ struct OpISV {
 template <bool FWD>
 struct OpIT {
     static constexpr int kind = K_DOWN;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<int, Q>& a, const int (&n0)[Q],
                                                  const int (&n1)[Q], const LevelCtx& x) {
         int c0r[Q], c2r[Q], n0r[Q];
-        right_nb(a.c[0], c0r, x.right);
-        right_nb(a.c[2], c2r, x.right);
-        right_nb(n0, n0r, x.right);
+        right_nb<EDGE>(a.c[0], c0r, x.right);
+        right_nb<EDGE>(a.c[2], c2r, x.right);
+        right_nb<EDGE>(n0, n0r, x.right);
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             if (FWD)
                 i_T_fwd(a.c[1][j], a.c[2][j], a.c[3][j], a.c[0][j], c0r[j], c2r[j], n0[j], n1[j],
-                        n0r[j], x.ha, x.va);
+                        n0r[j], hact<EDGE>(x), vact<EDGE>(x));
             else
                 i_T_inv(a.c[1][j], a.c[2][j], a.c[3][j], a.c[0][j], c0r[j], c2r[j], n0[j], n1[j],
-                        n0r[j], x.ha, x.va);
+                        n0r[j], hact<EDGE>(x), vact<EDGE>(x));
         }
     }
 };
@@ -313,92 +330,132 @@ template <bool FWD>
 struct OpIS {
     static constexpr int kind = K_UP;
     static constexpr bool kHsub = true;
-    template <int Q>
+    template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<int, Q>& a, const int (&up2)[Q],
                                                  const int (&up3)[Q], const LevelCtx& x) {
         int c1l[Q], c3l[Q], u3l[Q];
-        left_nb(a.c[1], c1l, x.left);
-        left_nb(a.c[3], c3l, x.left);
-        left_nb(up3, u3l, x.left);
+        left_nb<EDGE>(a.c[1], c1l, x.left);
+        left_nb<EDGE>(a.c[3], c3l, x.left);
+        left_nb<EDGE>(up3, u3l, x.left);
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             if (FWD)
                 i_S_fwd(a.c[0][j], a.c[1][j], a.c[2][j], a.c[3][j], c1l[j], c3l[j], up2[j], up3[j],
-                        u3l[j], x.ha, x.va);
+                        u3l[j], hact<EDGE>(x), vact<EDGE>(x));
             else
                 i_S_inv(a.c[0][j], a.c[1][j], a.c[2][j], a.c[3][j], c1l[j], c3l[j], up2[j], up3[j],
-                        u3l[j], x.ha, x.va);
+                        u3l[j], hact<EDGE>(x), vact<EDGE>(x));
         }
     }
 };
 
 // ---------------------------------------------------------------- stages ----
+// A stage consumes a block of RB consecutive quadruple rows at a time.  Doing
+// every lifting step on the whole block before the next step gives each lane
+// RB x Q independent quadruples per step; the stage keeps only one row (or the
+// odd half of one row) from the previous block.
+template <class T, int Q, int RB>
+struct Block {
+    Quads<T, Q> r[RB];
+};
+
 template <class T, int Q, int KIND>
 struct StageState {};
 template <class T, int Q>
 struct StageState<T, Q, K_DOWN> {
-    Quads<T, Q> saved;  // the previous input row
+    Quads<T, Q> saved;  // the last input row of the previous block (pre-step)
 };
 template <class T, int Q>
 struct StageState<T, Q, K_UP> {
-    T p2[Q], p3[Q];  // odd-row components of the previous input row (pre-step, mirrored)
-    bool primed;
+    T p2[Q], p3[Q];  // odd-row components of the previous block's last row (pre-step, mirrored)
 };
 
-template <class T, int Q, class Op>
-__device__ __forceinline__ void run_stage(StageState<T, Q, K_NONE>&, Quads<T, Q>& a, int&,
+template <bool EDGE, class T, int Q, int RB, class Op>
+__device__ __forceinline__ void run_stage(StageState<T, Q, K_NONE>&, Block<T, Q, RB>& b, int&,
                                           const LevelCtx& x) {
-    Op::apply(a, x);
+#pragma unroll
+    for (int j = 0; j < RB; ++j) Op::template apply<EDGE>(b.r[j], x);
 }
 
-// A predict reading the lower row: emits row r-1 when row r arrives.
-template <class T, int Q, class Op>
-__device__ __forceinline__ void run_stage(StageState<T, Q, K_DOWN>& st, Quads<T, Q>& a, int& r,
+// A predict reading the lower row.  Input rows [r0, r0 + RB); output rows
+// [r0 - 1, r0 + RB - 1): row r0 - 1 (kept from the last block) completes now and
+// the last input row waits for the next block.
+template <bool EDGE, class T, int Q, int RB, class Op>
+__device__ __forceinline__ void run_stage(StageState<T, Q, K_DOWN>& st, Block<T, Q, RB>& b, int& r0,
                                           const LevelCtx& x) {
-    Quads<T, Q> out = st.saved;
-    const bool real = r < x.ne_r;  // else row r is the mirror of row r-1
-    T n0[Q], n1[Q];
+    const Quads<T, Q> keep = b.r[RB - 1];
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-        n0[j] = real ? a.c[0][j] : out.c[0][j];
-        n1[j] = real ? a.c[1][j] : out.c[1][j];
+    for (int j = RB - 1; j >= 0; --j) {
+        Quads<T, Q> o = (j > 0) ? b.r[j - 1] : st.saved;  // output row r0 - 1 + j
+        T n0[Q], n1[Q];                                     // its lower row, pre-step
+        // the lower row is past the last even row: mirror (the row itself)
+        const bool real = !EDGE || (r0 + j) < x.ne_r;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            n0[i] = real ? b.r[j].c[0][i] : o.c[0][i];
+            n1[i] = real ? b.r[j].c[1][i] : o.c[1][i];
+        }
+        Op::template apply<EDGE>(o, n0, n1, x);
+        b.r[j] = o;
     }
-    st.saved = a;
-    Op::apply(out, n0, n1, x);
-    a = out;
-    r = r - 1;
+    st.saved = keep;
+    r0 -= 1;
 }
 
-// An update reading the upper row: emits row r at once.
-template <class T, int Q, class Op>
-__device__ __forceinline__ void run_stage(StageState<T, Q, K_UP>& st, Quads<T, Q>& a, int& r,
+// An update reading the upper row.  Input and output rows [r0, r0 + RB).
+template <bool EDGE, class T, int Q, int RB, class Op>
+__device__ __forceinline__ void run_stage(StageState<T, Q, K_UP>& st, Block<T, Q, RB>& b, int& r0,
                                           const LevelCtx& x) {
-    if (st.primed && r >= x.no_r) {  // odd height: the last row has no odd image row
-        copy_arr(a.c[2], st.p2);
-        copy_arr(a.c[3], st.p3);
-    }
-    if (Op::kHsub && x.need_hsub) {
-        subst_odd(a.c[1], x.odd);
-        subst_odd(a.c[3], x.odd);
-    }
-    T up2[Q], up3[Q];
-    const bool use_prev = st.primed && r != 0;
+    if (EDGE) {
+        if (Op::kHsub && x.need_hsub) {
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-        up2[j] = use_prev ? st.p2[j] : a.c[2][j];
-        up3[j] = use_prev ? st.p3[j] : a.c[3][j];
+            for (int j = 0; j < RB; ++j) {
+                subst_odd(b.r[j].c[1], x.odd);
+                subst_odd(b.r[j].c[3], x.odd);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+            if (r0 + j >= x.no_r) {  // odd height: the last row has no odd image row
+                if (j > 0) {
+                    copy_arr(b.r[j].c[2], b.r[j - 1].c[2]);
+                    copy_arr(b.r[j].c[3], b.r[j - 1].c[3]);
+                } else {
+                    copy_arr(b.r[j].c[2], st.p2);
+                    copy_arr(b.r[j].c[3], st.p3);
+                }
+            }
+        }
     }
-    copy_arr(st.p2, a.c[2]);
-    copy_arr(st.p3, a.c[3]);
-    st.primed = true;
-    Op::apply(a, up2, up3, x);
+    T n2[Q], n3[Q];
+    copy_arr(n2, b.r[RB - 1].c[2]);
+    copy_arr(n3, b.r[RB - 1].c[3]);
+#pragma unroll
+    for (int j = RB - 1; j >= 0; --j) {  // downwards: the upper row is still pre-step
+        T up2[Q], up3[Q];
+        if (j > 0) {
+            copy_arr(up2, b.r[j - 1].c[2]);
+            copy_arr(up3, b.r[j - 1].c[3]);
+        } else {
+            copy_arr(up2, st.p2);
+            copy_arr(up3, st.p3);
+        }
+        if (EDGE && r0 + j == 0) {  // image top: the upper row is the row itself
+            copy_arr(up2, b.r[j].c[2]);
+            copy_arr(up3, b.r[j].c[3]);
+        }
+        Op::template apply<EDGE>(b.r[j], up2, up3, x);
+    }
+    copy_arr(st.p2, n2);
+    copy_arr(st.p3, n3);
 }
 
 template <class T, int Q, class... Ops>
 struct Chain {
     static constexpr int LAG = 0;
     __device__ __forceinline__ void init() {}
-    __device__ __forceinline__ void push(Quads<T, Q>&, int&, const LevelCtx&) {}
+    template <bool EDGE, int RB>
+    __device__ __forceinline__ void push(Block<T, Q, RB>&, int&, const LevelCtx&) {}
 };
 template <class T, int Q, class Op, class... Rest>
 struct Chain<T, Q, Op, Rest...> {
@@ -409,9 +466,10 @@ struct Chain<T, Q, Op, Rest...> {
         zero(st);
         rest.init();
     }
-    __device__ __forceinline__ void push(Quads<T, Q>& a, int& r, const LevelCtx& x) {
-        run_stage<T, Q, Op>(st, a, r, x);
-        rest.push(a, r, x);
+    template <bool EDGE, int RB>
+    __device__ __forceinline__ void push(Block<T, Q, RB>& b, int& r0, const LevelCtx& x) {
+        run_stage<EDGE, T, Q, RB, Op>(st, b, r0, x);
+        rest.template push<EDGE, RB>(b, r0, x);
     }
 
    private:
@@ -425,12 +483,10 @@ struct Chain<T, Q, Op, Rest...> {
     __device__ __forceinline__ static void zero(StageState<T, Q, K_UP>& s) {
 #pragma unroll
         for (int j = 0; j < Q; ++j) s.p2[j] = s.p3[j] = T(0);
-        s.primed = false;
     }
 };
 
 // The op chains of every (element type, scheme, direction).
-
 template <class T, int Q, int SCH, bool FWD>
 struct Pipe;
 
@@ -493,6 +549,10 @@ struct Pipe<int, Q, SCH_RED, false> {
     using type = Chain<int, Q, OpIS<false>, OpIT<false>>;
 };
 
+// CDF 9/7 scale of LL, HL, LH, HH when both axes are active: 1/K^2, 1, 1, K^2.
+constexpr float kScaleLL = 1.0f / (kK * kK);
+constexpr float kScaleHH = kK * kK;
+
 // One level of the transform for one warp: the chain plus the 9/7 scaling.
 template <class T, int Q, int SCH, bool FWD>
 struct Engine {
@@ -504,22 +564,51 @@ struct Engine {
         chain.init();
         npush = 0;
     }
-    // Push row r; on return `a` / `r` hold the emitted row.  Returns false
-    // while the pipeline is still filling.
-    __device__ __forceinline__ bool push(Quads<T, Q>& a, int& r, const LevelCtx& x) {
-        if (!FWD) scale(a, x);
-        chain.push(a, r, x);
-        if (FWD) scale(a, x);
+    // Push input rows [r0, r0 + RB); on return `b` holds the emitted rows
+    // [r0 - LAG, r0 - LAG + RB) (garbage while the pipeline fills).
+    template <bool EDGE, int RB>
+    __device__ __forceinline__ void push(Block<T, Q, RB>& b, int r0, const LevelCtx& x) {
+        if (!FWD) {
+#pragma unroll
+            for (int j = 0; j < RB; ++j) scale<EDGE>(b.r[j], x);
+        }
+        chain.template push<EDGE, RB>(b, r0, x);
+        if (FWD) {
+#pragma unroll
+            for (int j = 0; j < RB; ++j) scale<EDGE>(b.r[j], x);
+        }
+    }
+    // One row; returns false while the pipeline is still filling, and sets r to
+    // the emitted row.
+    template <bool EDGE>
+    __device__ __forceinline__ bool push_counted(Quads<T, Q>& a, int& r, const LevelCtx& x) {
+        Block<T, Q, 1> b;
+        b.r[0] = a;
+        push<EDGE, 1>(b, r, x);
+        a = b.r[0];
+        r -= LAG;
         return ++npush > LAG;
     }
 
    private:
+    template <bool EDGE>
     __device__ __forceinline__ static void scale(Quads<int, Q>&, const LevelCtx&) {}
+    template <bool EDGE>
     __device__ __forceinline__ static void scale(Quads<float, Q>& a, const LevelCtx& x) {
+        if (EDGE) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int j = 0; j < Q; ++j) a.c[k][j] *= x.s[k];
+                for (int j = 0; j < Q; ++j) a.c[k][j] *= x.s[k];
+        } else {
+            // both axes active: HL and LH keep their scale 1
+            const float sll = FWD ? kScaleLL : kScaleHH, shh = FWD ? kScaleHH : kScaleLL;
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                a.c[0][j] *= sll;
+                a.c[3][j] *= shh;
+            }
+        }
     }
 };
 

@@ -105,22 +105,127 @@ __device__ __forceinline__ void pair_rows(const T (&e)[Q], const T (&o)[Q], Quad
     }
 }
 
-template <class T, int SCH, int NL>
-__global__ void __launch_bounds__(kFwdWarps * 32)
+__host__ __device__ constexpr int floordiv2(int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
+
+// All state of one warp's work item: the level engines, per-level geometry and
+// the pending even LL rows, plus the static per-slot schedule.  Q1 quadruple
+// columns per lane at level 1 (2 Q1 pixels), Q1/2 at level 2, Q1/4 at level 3.
+template <class T, int SCH, int NL, int Q1>
+struct FwdWarp {
+    static constexpr int LAG = std::is_same<T, float>::value ? 2 : 1;
+    static constexpr int Q2 = Q1 / 2 > 0 ? Q1 / 2 : 1;
+    static constexpr int Q3 = Q1 / 4 > 0 ? Q1 / 4 : 1;
+    static constexpr int BW = 64 * Q1;  // box width in pixels
+    Engine<T, Q1, SCH, true> e1;
+    Engine<T, Q2, SCH, true> e2;
+    Engine<T, Q3, SCH, true> e3;
+    LevelCtx x1, x2, x3;
+    StoreGeo s1, s2, s3;
+    T pend1[Q1], pend2[Q2];
+    T* mallat;
+    T* ll;
+    long long mpitch, llpitch;
+    bool lane_ok, vec_ll;
+    int lane;
+
+    // One slot: level-1 input quadruple rows q0 .. q0+3 (q0 a multiple of 4) in
+    // shared memory (8 image rows of BW pixels), pushed as one block.  With
+    // q0 % 4 == 0 the rows every level emits, and how LL rows pair into the
+    // next level's quadruple rows, are fixed by the pipeline lag alone.
+    template <bool EDGE>
+    __device__ __forceinline__ void slot(const T* sm, int q0) {
+        using V4 = typename VecOf<T, 4>::type;
+        Block<T, Q1, 4> b1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            Quads<T, Q1>& row = b1.r[k];
+#pragma unroll
+            for (int i = 0; i < Q1 / 2; ++i) {
+                const V4 a = reinterpret_cast<const V4*>(sm + (2 * k) * BW + 2 * Q1 * lane)[i];
+                const V4 c = reinterpret_cast<const V4*>(sm + (2 * k + 1) * BW + 2 * Q1 * lane)[i];
+                row.c[0][2 * i] = a.x; row.c[1][2 * i] = a.y;
+                row.c[0][2 * i + 1] = a.z; row.c[1][2 * i + 1] = a.w;
+                row.c[2][2 * i] = c.x; row.c[3][2 * i] = c.y;
+                row.c[2][2 * i + 1] = c.z; row.c[3][2 * i + 1] = c.w;
+            }
+        }
+        e1.template push<EDGE, 4>(b1, q0, x1);
+        const int r1 = q0 - LAG;  // first emitted level-1 row
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            store_details<T, Q1>(b1.r[k], r1 + k, s1, mallat, mpitch, lane_ok);
+            if constexpr (NL == 1) store_ll<T, Q1>(b1.r[k], r1 + k, s1, ll, llpitch, lane_ok, vec_ll);
+        }
+        if constexpr (NL >= 2) {
+            // level-2 input rows q0/2 - 1 and q0/2 = LL rows q0 - 2 .. q0 + 1
+            Block<T, Q2, 2> b2;
+            if constexpr (LAG == 2) {  // emitted rows q0-2 .. q0+1
+                pair_rows<T, Q1>(b1.r[0].c[0], b1.r[1].c[0], b2.r[0]);
+                pair_rows<T, Q1>(b1.r[2].c[0], b1.r[3].c[0], b2.r[1]);
+            } else {  // emitted rows q0-1 .. q0+2; row q0-2 was kept from the last slot
+                pair_rows<T, Q1>(pend1, b1.r[0].c[0], b2.r[0]);
+                pair_rows<T, Q1>(b1.r[1].c[0], b1.r[2].c[0], b2.r[1]);
+                copy_arr(pend1, b1.r[3].c[0]);
+            }
+            const int in2 = q0 / 2 - 1;
+            e2.template push<EDGE, 2>(b2, in2, x2);
+            const int r2 = in2 - LAG;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                store_details<T, Q2>(b2.r[k], r2 + k, s2, mallat, mpitch, lane_ok);
+                if constexpr (NL == 2) store_ll<T, Q2>(b2.r[k], r2 + k, s2, ll, llpitch, lane_ok, vec_ll);
+            }
+            if constexpr (NL >= 3) {
+                static_assert(Q1 >= 4, "three fused levels need 4 columns per lane");
+                Block<T, Q3, 1> b3;
+                int in3;
+                if constexpr (LAG == 2) {  // level-2 rows q0/2-3, q0/2-2; q0/2-4 kept
+                    pair_rows<T, Q2>(pend2, b2.r[0].c[0], b3.r[0]);
+                    copy_arr(pend2, b2.r[1].c[0]);
+                    in3 = q0 / 4 - 2;
+                } else {  // level-2 rows q0/2-2, q0/2-1
+                    pair_rows<T, Q2>(b2.r[0].c[0], b2.r[1].c[0], b3.r[0]);
+                    in3 = q0 / 4 - 1;
+                }
+                e3.template push<EDGE, 1>(b3, in3, x3);
+                store_details<T, Q3>(b3.r[0], in3 - LAG, s3, mallat, mpitch, lane_ok);
+                store_ll<T, Q3>(b3.r[0], in3 - LAG, s3, ll, llpitch, lane_ok, vec_ll);
+            }
+        }
+    }
+};
+
+// Rows of level l pushed in the slot of level-1 rows [q0, q0 + 4) lie in
+// [lo, hi]; the interior code is valid if every stage row touched is at least
+// one row away from the top and stays clear of the last odd row.
+__device__ __forceinline__ bool rows_interior(int q0, int nl, int lag, const int* no_r) {
+    int lo = q0, hi = q0 + 3;
+    for (int l = 0; l < nl; ++l) {
+        if (lo - lag - 1 < 0 || hi + 1 >= no_r[l]) return false;
+        lo = floordiv2(lo - lag) - 1;
+        hi = floordiv2(hi - lag);
+    }
+    return true;
+}
+
+template <int Q1>
+__host__ __device__ constexpr int fwd_min_blocks() { return Q1 <= 2 ? 4 : 2; }
+
+template <class T, int SCH, int NL, int Q1>
+__global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
     fwd_fused_kernel(const __grid_constant__ CUtensorMap map, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    constexpr int RHO = std::is_same<T, float>::value ? 2 : 1;
-    using E1 = Engine<T, 4, SCH, true>;
-    using E2 = Engine<T, 2, SCH, true>;
-    using E3 = Engine<T, 1, SCH, true>;
-    static_assert(E1::LAG == RHO && E2::LAG == RHO && E3::LAG == RHO, "lag");
+    using FW = FwdWarp<T, SCH, NL, Q1>;
+    constexpr int RHO = FW::LAG;
+    constexpr int BW = FW::BW;
+    static_assert(Engine<T, Q1, SCH, true>::LAG == RHO && Engine<T, 1, SCH, true>::LAG == RHO, "lag");
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wid = blockIdx.x * kFwdWarps + warp;
     if (wid >= a.nstrips * a.nsegs) return;
 
-    constexpr int kSlotElems = kFwdSlotRows * kBoxW;
+    constexpr int kSlotElems = kFwdSlotRows * BW;
     T* ring = reinterpret_cast<T*>(smem_raw) + (size_t)warp * kFwdSlots * kSlotElems;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kFwdWarps * kFwdSlots *
                                                               kSlotElems * sizeof(T)) +
@@ -129,7 +234,6 @@ __global__ void __launch_bounds__(kFwdWarps * 32)
     const int strip = wid % a.nstrips;
     const int seg = wid / a.nstrips;
     const int xb = strip * a.valid_px - a.xoff;
-    const bool lane_ok = lane >= a.lane_lo && lane < a.lane_hi;
 
     // rows of the last fused level this item produces, and the input rows it needs
     const int neN = (a.lv[NL - 1].h + 1) >> 1;
@@ -145,41 +249,45 @@ __global__ void __launch_bounds__(kFwdWarps * 32)
             e = 2 * e + 1;
         }
     }
-    const int qstart = max(f, 0);
+    const int qstart = max(f, 0) & ~3;  // slots hold 4 quadruple rows, aligned
     const int qend = e + 1;
-    const int nslots = (2 * (qend - qstart) + kFwdSlotRows - 1) / kFwdSlotRows;
+    const int nslots = (qend - qstart + 3) / 4;
 
-    // per-level lane geometry
-    const int g1 = (xb >> 1) + 4 * lane;
-    const LevelCtx x1 = make_ctx(g1, 4, a.lv[0].h, a.lv[0].w, a.lane_lo, a.lane_hi, a.lv[0].s);
-    const StoreGeo s1 = make_geo(a.lv[0].h, a.lv[0].w, g1, 4, R0 << (NL - 1), R1 << (NL - 1),
-                                 a.mallat_pitch);
-    LevelCtx x2, x3;
-    StoreGeo s2, s3;
+    FW W;
+    W.lane = lane;
+    W.lane_ok = lane >= a.lane_lo && lane < a.lane_hi;
+    W.mallat = reinterpret_cast<T*>(a.mallat);
+    W.mpitch = a.mallat_pitch;
+    W.ll = reinterpret_cast<T*>(a.ll);
+    W.llpitch = a.ll_pitch;
+    constexpr int QN = NL == 1 ? Q1 : (NL == 2 ? FW::Q2 : FW::Q3);
+    W.vec_ll = (a.ll_pitch % QN) == 0;
+    int no_r[3] = {0, 0, 0};
+    bool hfast = true;
+    {
+        const int g1 = (xb >> 1) + Q1 * lane;
+        W.x1 = make_ctx(g1, Q1, a.lv[0].h, a.lv[0].w, a.lane_lo, a.lane_hi, a.lv[0].s);
+        W.s1 = make_geo(a.lv[0].h, a.lv[0].w, g1, Q1, R0 << (NL - 1), R1 << (NL - 1), a.mallat_pitch);
+        no_r[0] = a.lv[0].h >> 1;
+        hfast = hfast && (xb >> 1) >= 2 && (xb >> 1) + 32 * Q1 + 2 <= (a.lv[0].w >> 1);
+    }
     if constexpr (NL >= 2) {
-        const int g2 = (xb >> 2) + 2 * lane;
-        x2 = make_ctx(g2, 2, a.lv[1].h, a.lv[1].w, a.lane_lo, a.lane_hi, a.lv[1].s);
-        s2 = make_geo(a.lv[1].h, a.lv[1].w, g2, 2, R0 << (NL - 2), R1 << (NL - 2), a.mallat_pitch);
+        const int g2 = (xb >> 2) + FW::Q2 * lane;
+        W.x2 = make_ctx(g2, FW::Q2, a.lv[1].h, a.lv[1].w, a.lane_lo, a.lane_hi, a.lv[1].s);
+        W.s2 = make_geo(a.lv[1].h, a.lv[1].w, g2, FW::Q2, R0 << (NL - 2), R1 << (NL - 2), a.mallat_pitch);
+        no_r[1] = a.lv[1].h >> 1;
+        hfast = hfast && (xb >> 2) >= 2 && (xb >> 2) + 32 * FW::Q2 + 2 <= (a.lv[1].w >> 1);
     }
     if constexpr (NL >= 3) {
-        const int g3 = (xb >> 3) + lane;
-        x3 = make_ctx(g3, 1, a.lv[2].h, a.lv[2].w, a.lane_lo, a.lane_hi, a.lv[2].s);
-        s3 = make_geo(a.lv[2].h, a.lv[2].w, g3, 1, R0, R1, a.mallat_pitch);
+        const int g3 = (xb >> 3) + FW::Q3 * lane;
+        W.x3 = make_ctx(g3, FW::Q3, a.lv[2].h, a.lv[2].w, a.lane_lo, a.lane_hi, a.lv[2].s);
+        W.s3 = make_geo(a.lv[2].h, a.lv[2].w, g3, FW::Q3, R0, R1, a.mallat_pitch);
+        no_r[2] = a.lv[2].h >> 1;
+        hfast = hfast && (xb >> 3) >= 2 && (xb >> 3) + 32 * FW::Q3 + 2 <= (a.lv[2].w >> 1);
     }
-    constexpr int QN = 4 >> (NL - 1);
-    const bool vec_ll = (a.ll_pitch % QN) == 0;
-
-    T* mallat = reinterpret_cast<T*>(a.mallat);
-    T* ll = reinterpret_cast<T*>(a.ll);
-
-    E1 e1;
-    E2 e2;
-    E3 e3;
-    e1.init();
-    if constexpr (NL >= 2) e2.init();
-    if constexpr (NL >= 3) e3.init();
-    T pend1[4], pend2[2];
-    int pend1_r = -0x40000000, pend2_r = -0x40000000;
+    W.e1.init();
+    if constexpr (NL >= 2) W.e2.init();
+    if constexpr (NL >= 3) W.e3.init();
 
     // ---- TMA ring prologue
     const uint32_t ring_s = smem_u32(ring);
@@ -196,7 +304,6 @@ __global__ void __launch_bounds__(kFwdWarps * 32)
     }
     __syncwarp();
 
-    int q = qstart;
     bool failed = false;
     int s = 0;
     for (; s < nslots; ++s) {
@@ -206,54 +313,11 @@ __global__ void __launch_bounds__(kFwdWarps * 32)
             failed = true;
             break;
         }
-        const T* slot = ring + b * kSlotElems;
-#pragma unroll 1
-        for (int k = 0; k < kFwdSlotRows / 2 && q < qend; ++k, ++q) {
-            using V4 = typename VecOf<T, 4>::type;
-            const V4* r0 = reinterpret_cast<const V4*>(slot + (2 * k) * kBoxW + kLanePx * lane);
-            const V4* r1 = reinterpret_cast<const V4*>(slot + (2 * k + 1) * kBoxW + kLanePx * lane);
-            const V4 a0 = r0[0], a1 = r0[1], b0 = r1[0], b1 = r1[1];
-            Quads<T, 4> row;
-            row.c[0][0] = a0.x; row.c[1][0] = a0.y; row.c[0][1] = a0.z; row.c[1][1] = a0.w;
-            row.c[0][2] = a1.x; row.c[1][2] = a1.y; row.c[0][3] = a1.z; row.c[1][3] = a1.w;
-            row.c[2][0] = b0.x; row.c[3][0] = b0.y; row.c[2][1] = b0.z; row.c[3][1] = b0.w;
-            row.c[2][2] = b1.x; row.c[3][2] = b1.y; row.c[2][3] = b1.z; row.c[3][3] = b1.w;
-
-            int r1i = q;
-            if (!e1.push(row, r1i, x1)) continue;
-            store_details<T, 4>(row, r1i, s1, mallat, a.mallat_pitch, lane_ok);
-            if constexpr (NL == 1) {
-                store_ll<T, 4>(row, r1i, s1, ll, a.ll_pitch, lane_ok, vec_ll);
-            } else {
-                if ((r1i & 1) == 0) {
-                    copy_arr(pend1, row.c[0]);
-                    pend1_r = r1i;
-                    continue;
-                }
-                if (pend1_r != r1i - 1) continue;
-                Quads<T, 2> row2;
-                pair_rows<T, 4>(pend1, row.c[0], row2);
-                int r2i = r1i >> 1;
-                if (!e2.push(row2, r2i, x2)) continue;
-                store_details<T, 2>(row2, r2i, s2, mallat, a.mallat_pitch, lane_ok);
-                if constexpr (NL == 2) {
-                    store_ll<T, 2>(row2, r2i, s2, ll, a.ll_pitch, lane_ok, vec_ll);
-                } else {
-                    if ((r2i & 1) == 0) {
-                        copy_arr(pend2, row2.c[0]);
-                        pend2_r = r2i;
-                        continue;
-                    }
-                    if (pend2_r != r2i - 1) continue;
-                    Quads<T, 1> row3;
-                    pair_rows<T, 2>(pend2, row2.c[0], row3);
-                    int r3i = r2i >> 1;
-                    if (!e3.push(row3, r3i, x3)) continue;
-                    store_details<T, 1>(row3, r3i, s3, mallat, a.mallat_pitch, lane_ok);
-                    store_ll<T, 1>(row3, r3i, s3, ll, a.ll_pitch, lane_ok, vec_ll);
-                }
-            }
-        }
+        const int q0 = qstart + 4 * s;
+        if (hfast && rows_interior(q0, NL, RHO, no_r))
+            W.template slot<false>(ring + b * kSlotElems, q0);
+        else
+            W.template slot<true>(ring + b * kSlotElems, q0);
         __syncwarp();
         if (lane == 0 && s + kFwdSlots < nslots) {
             fence_proxy_async_smem();
@@ -270,16 +334,16 @@ __global__ void __launch_bounds__(kFwdWarps * 32)
     }
 }
 
-size_t fwd_smem_bytes(int elem_bytes) {
-    return (size_t)kFwdWarps * kFwdSlots * kFwdSlotRows * kBoxW * elem_bytes +
+size_t fwd_smem_bytes(int elem_bytes, int q1) {
+    return (size_t)kFwdWarps * kFwdSlots * kFwdSlotRows * (64 * q1) * elem_bytes +
            (size_t)kFwdWarps * kFwdSlots * 8;
 }
 
-template <class T, int SCH, int NL>
+template <class T, int SCH, int NL, int Q1>
 static cudaError_t launch_one(const CUtensorMap& map, const FusedArgs& a, int grid,
                               cudaStream_t st) {
-    auto k = fwd_fused_kernel<T, SCH, NL>;
-    const size_t smem = fwd_smem_bytes(sizeof(T));
+    auto k = fwd_fused_kernel<T, SCH, NL, Q1>;
+    const size_t smem = fwd_smem_bytes(sizeof(T), Q1);
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     k<<<grid, kFwdWarps * 32, smem, st>>>(map, a);
@@ -287,31 +351,38 @@ static cudaError_t launch_one(const CUtensorMap& map, const FusedArgs& a, int gr
 }
 
 template <class T, int SCH>
-static cudaError_t launch_nl(int nl, const CUtensorMap& map, const FusedArgs& a, int grid,
+static cudaError_t launch_nl(int nl, int q1, const CUtensorMap& map, const FusedArgs& a, int grid,
                              cudaStream_t st) {
+    if (q1 == 2) {
+        switch (nl) {
+            case 1: return launch_one<T, SCH, 1, 2>(map, a, grid, st);
+            case 2: return launch_one<T, SCH, 2, 2>(map, a, grid, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (nl) {
-        case 1: return launch_one<T, SCH, 1>(map, a, grid, st);
-        case 2: return launch_one<T, SCH, 2>(map, a, grid, st);
-        case 3: return launch_one<T, SCH, 3>(map, a, grid, st);
+        case 1: return launch_one<T, SCH, 1, 4>(map, a, grid, st);
+        case 2: return launch_one<T, SCH, 2, 4>(map, a, grid, st);
+        case 3: return launch_one<T, SCH, 3, 4>(map, a, grid, st);
     }
     return cudaErrorInvalidValue;
 }
 
 template <class T>
-static cudaError_t launch_sch(int sch, int nl, const CUtensorMap& map, const FusedArgs& a,
+static cudaError_t launch_sch(int sch, int nl, int q1, const CUtensorMap& map, const FusedArgs& a,
                               int grid, cudaStream_t st) {
     switch (sch) {
-        case SCH_SEP: return launch_nl<T, SCH_SEP>(nl, map, a, grid, st);
-        case SCH_NONSEP: return launch_nl<T, SCH_NONSEP>(nl, map, a, grid, st);
-        case SCH_RED: return launch_nl<T, SCH_RED>(nl, map, a, grid, st);
+        case SCH_SEP: return launch_nl<T, SCH_SEP>(nl, q1, map, a, grid, st);
+        case SCH_NONSEP: return launch_nl<T, SCH_NONSEP>(nl, q1, map, a, grid, st);
+        case SCH_RED: return launch_nl<T, SCH_RED>(nl, q1, map, a, grid, st);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_fwd_fused(int elem, int scheme, int nl, const CUtensorMap& map,
+cudaError_t launch_fwd_fused(int elem, int scheme, int nl, int q1, const CUtensorMap& map,
                              const FusedArgs& a, int grid, cudaStream_t st) {
-    if (elem == 0) return launch_sch<float>(scheme, nl, map, a, grid, st);
-    return launch_sch<int>(scheme, nl, map, a, grid, st);
+    if (elem == 0) return launch_sch<float>(scheme, nl, q1, map, a, grid, st);
+    return launch_sch<int>(scheme, nl, q1, map, a, grid, st);
 }
 
 }  // namespace dwt

@@ -58,14 +58,13 @@ struct PassArgs {
 
 // Kernel-geometry constants of the streaming forward kernel.
 constexpr int kFwdWarps = 4;        // warps per CTA (each warp is independent)
-constexpr int kFwdSlots = 4;        // TMA ring depth per warp
-constexpr int kFwdSlotRows = 4;     // image rows per TMA box
-constexpr int kBoxW = 256;          // pixels per box row = 32 lanes x 8 pixels
-constexpr int kLanePx = 8;          // pixels per lane at level 1 (4 quadruple columns)
+constexpr int kFwdSlots = 3;        // TMA ring depth per warp
+constexpr int kFwdSlotRows = 8;     // image rows per TMA box (4 quadruple rows)
 
-size_t fwd_smem_bytes(int elem_bytes);
+size_t fwd_smem_bytes(int elem_bytes, int q1);
 
-cudaError_t launch_fwd_fused(int elem, int scheme, int nl, const CUtensorMap& map,
+// q1: quadruple columns per lane at the first fused level (2 or 4; 3 fused levels need 4)
+cudaError_t launch_fwd_fused(int elem, int scheme, int nl, int q1, const CUtensorMap& map,
                              const FusedArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_inv_fused(int elem, int scheme, int nl, const FusedArgs& a, int grid,
                              cudaStream_t st);

@@ -112,7 +112,7 @@ struct InvWarp {
         constexpr int Q = 4 >> (L - 1);
         load_details<T, Q>(a, i, g[L - 1], mallat, pitch);
         int r = i;
-        if (!eng<L>().push(a, r, x[L - 1])) return;
+        if (!eng<L>().template push_counted<true>(a, r, x[L - 1])) return;
         // emitted quadruple row r -> rows 2r (c0 c1 interleaved) and 2r+1 (c2 c3)
         if constexpr (L == 1) {
             if (!lane_ok || r < A0 || r >= A1) return;

@@ -23,6 +23,8 @@ SHAPES_LEVELS = [
     ((8, 8), 1), ((8, 8), 3), ((7, 9), 2), ((9, 7), 3), ((1, 9), 2), ((9, 1), 2), ((1, 1), 2),
     ((2, 2), 1), ((3, 3), 2), ((33, 70), 3), ((64, 300), 4), ((130, 257), 5), ((40, 513), 3),
     ((512, 512), 1), ((512, 512), 5), ((65, 1000), 6), ((301, 497), 4),
+    # wide and tall enough for the interior (border-free) code path at every fused level
+    ((1030, 2050), 5), ((2048, 1536), 3), ((777, 3001), 2),
 ]
 
 
