@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", type=int, default=8192,
+                    help="image side (profiling runs use a smaller case; the metric is 8192)")
     return ap.parse_args()
 
 
@@ -240,7 +243,9 @@ def run_reference(args, ws, rank):
 
 
 def main():
+    global H, W
     args = parse()
+    H = W = args.size
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
@@ -335,6 +340,10 @@ def main():
     if not args.no_variants:
         out["variants"] = variants(D, synth, dev, stream, x, dst)
 
+    if args.no_e2e:
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
     # end to end through the host-buffer entry point (copies inside the timed region)
     hs = torch.from_numpy(x_h).pin_memory()
     hd = torch.empty_like(hs).pin_memory()

@@ -34,6 +34,7 @@ struct dwt2d_plan_s {
     int sm_count;
     int fwd_warps_target, inv_warps_target;
     int fwd_q1;  // quadruple columns per lane of the forward kernel (2 or 4)
+    int inv_q1;  // the same for the inverse
     int min_segq;
     // workspace layout (bytes from the start of the workspace)
     size_t off_a, off_b, off_x, off_y;
@@ -118,12 +119,12 @@ EncodeTiledFn encode_fn() {
 }
 
 dwt2d_status make_map(CUtensorMap* map, const void* base, int h, int w, long long pitch_elems,
-                      int elem, bool is_int, int box_w) {
+                      int elem, bool is_int, int box_w, int box_h = kFwdSlotRows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return DWT2D_ERR_CUDA;
     const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
     const cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * elem)};
-    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)kFwdSlotRows};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = fn(map, is_int ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                           2, const_cast<void*>(base), dims, strides, box, estr,
@@ -238,10 +239,32 @@ dwt2d_status run_fused(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t
         a.out_pitch = last ? dst_pe : bpitch[k & 1];
         a.err = err;
         int grid;
-        decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, 4, p->inv_warps_target, &a, &grid, 4);
-        mark(p, k, 0, st);
-        if (launch_inv_fused(elem_kind, sch, g.n, a, grid, st) != cudaSuccess) return DWT2D_ERR_CUDA;
-        mark(p, k, 1, st);
+        if (g.n <= 2) {
+            // TMA ring: boxes of the Mallat array and of the LL source
+            const int q1 = p->inv_q1;
+            const int w1 = 32 * q1 + 4, w2 = 16 * q1 + 4;
+            const bool is_int = elem_kind == 1;
+            CUtensorMap m1, m2, ml;
+            dwt2d_status s = make_map(&m1, src, p->H, p->W, src_pe, p->elem, is_int, w1, 4);
+            if (s == DWT2D_OK) s = make_map(&m2, src, p->H, p->W, src_pe, p->elem, is_int, w2, 2);
+            const int llh = (a.lv[g.n - 1].h + 1) / 2, llw = (a.lv[g.n - 1].w + 1) / 2;
+            const bool ll_is_src = ll_in == src;
+            if (s == DWT2D_OK)
+                s = make_map(&ml, ll_in, ll_is_src ? p->H : llh, ll_is_src ? p->W : llw, ll_pitch,
+                             p->elem, is_int, g.n == 1 ? w1 : w2, g.n == 1 ? 4 : 2);
+            if (s != DWT2D_OK) return s;
+            decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, q1, p->inv_warps_target, &a, &grid,
+                      kInvTmaWarps);
+            mark(p, k, 0, st);
+            if (launch_inv_tma(elem_kind, sch, g.n, q1, m1, m2, ml, a, grid, st) != cudaSuccess)
+                return DWT2D_ERR_CUDA;
+            mark(p, k, 1, st);
+        } else {
+            decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, 4, p->inv_warps_target, &a, &grid, 4);
+            mark(p, k, 0, st);
+            if (launch_inv_fused(elem_kind, sch, g.n, a, grid, st) != cudaSuccess) return DWT2D_ERR_CUDA;
+            mark(p, k, 1, st);
+        }
         ll_in = a.out;
         ll_pitch = a.out_pitch;
     }
@@ -426,9 +449,10 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
     cudaGetLastError();
     p->sm_count = sms;
     p->fwd_warps_target = sms * env_int("DWT2D_FWD_WARPS_PER_SM", 16);
-    p->inv_warps_target = sms * env_int("DWT2D_INV_WARPS_PER_SM", 16);
+    p->inv_warps_target = sms * env_int("DWT2D_INV_WARPS_PER_SM", 12);
     p->min_segq = env_int("DWT2D_MIN_SEGQ", 2);
     p->fwd_q1 = env_int("DWT2D_FWD_Q", 2) == 4 ? 4 : 2;
+    p->inv_q1 = env_int("DWT2D_INV_Q", 2) == 4 ? 4 : 2;
 
     // workspace: header | LL buffer A | LL buffer B | (multipass) X | Y
     size_t off = kHeader;

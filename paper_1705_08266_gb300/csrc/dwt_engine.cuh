@@ -32,6 +32,23 @@ struct Quads {
     T c[4][Q];  // c[component][column within lane]
 };
 
+template <class T, int Q>
+struct VecOf;
+template <>
+struct VecOf<float, 4> { using type = float4; };
+template <>
+struct VecOf<float, 2> { using type = float2; };
+template <>
+struct VecOf<float, 1> { using type = float; };
+template <>
+struct VecOf<int, 4> { using type = int4; };
+template <>
+struct VecOf<int, 2> { using type = int2; };
+template <>
+struct VecOf<int, 1> { using type = int; };
+
+__host__ __device__ constexpr int floordiv2(int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
+
 // Per-level information of one lane (horizontal) and of the level (vertical).
 struct LevelCtx {
     unsigned right;  // bit j: column j has its right (even) neighbour inside the image

@@ -17,21 +17,6 @@
 
 namespace dwt {
 
-template <class T, int Q>
-struct VecOf;
-template <>
-struct VecOf<float, 4> { using type = float4; };
-template <>
-struct VecOf<float, 2> { using type = float2; };
-template <>
-struct VecOf<float, 1> { using type = float; };
-template <>
-struct VecOf<int, 4> { using type = int4; };
-template <>
-struct VecOf<int, 2> { using type = int2; };
-template <>
-struct VecOf<int, 1> { using type = int; };
-
 // Store Q consecutive values at p; `avail` columns remain inside the band.
 template <class T, int Q>
 __device__ __forceinline__ void store_cols(T* p, const T (&v)[Q], int avail, bool vec) {
@@ -104,8 +89,6 @@ __device__ __forceinline__ void pair_rows(const T (&e)[Q], const T (&o)[Q], Quad
         n.c[3][j] = o[2 * j + 1];
     }
 }
-
-__host__ __device__ constexpr int floordiv2(int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
 
 // All state of one warp's work item: the level engines, per-level geometry and
 // the pending even LL rows, plus the static per-slot schedule.  Q1 quadruple

@@ -69,6 +69,15 @@ cudaError_t launch_fwd_fused(int elem, int scheme, int nl, int q1, const CUtenso
 cudaError_t launch_inv_fused(int elem, int scheme, int nl, const FusedArgs& a, int grid,
                              cudaStream_t st);
 
+// TMA-fed inverse for 1 or 2 fused levels: m1 / m2 map the Mallat array with
+// boxes {32 q1 + 4, 4} and {16 q1 + 4, 2}; ml maps the LL source with the
+// level-1 box (1 level) or the level-2 box (2 levels).
+cudaError_t launch_inv_tma(int elem, int scheme, int nl, int q1, const CUtensorMap& m1,
+                           const CUtensorMap& m2, const CUtensorMap& ml, const FusedArgs& a,
+                           int grid, cudaStream_t st);
+size_t inv_tma_smem_bytes(int elem_bytes, int nl, int q1);
+constexpr int kInvTmaWarps = 4;
+
 // elem: 0 = float32, 1 = int32.  kind: the step (see dwt_multipass.cu).
 cudaError_t launch_pass(int elem, int kind, bool fwd, const PassArgs& a, cudaStream_t st);
 

@@ -1,0 +1,347 @@
+// Inverse transform: TMA-fed warp-streaming kernel, 1 or 2 levels per launch.
+//
+// Coarse to fine.  A warp owns a strip of output columns and a segment of
+// output rows.  Each slot of its shared-memory ring holds, for four level-1
+// quadruple rows, the three level-1 detail bands and (two fused levels) the
+// LL and three detail bands of the two level-2 rows that produce those
+// level-1 rows' LL values.  Every box is 2-D TMA; a box starts at the column
+// rounded down to 16 bytes and the lane reads from the remainder on.  The
+// level-2 engine runs LAG + RHO rows ahead of level 1 (its first slots of a
+// work item load and push level 2 only), so the LL rows it hands down are
+// exact from the first level-1 row of the item on.
+#include <type_traits>
+
+#include "dwt_engine.cuh"
+#include "dwt_internal.h"
+#include "dwt_tma.cuh"
+
+namespace dwt {
+
+constexpr int kInvWarps = 4;  // warps per CTA (independent)
+constexpr int kInvSlots = 3;  // ring depth per warp
+
+__host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }
+
+template <class T, int NL, int Q1>
+struct InvLayout {
+    static constexpr int Q2 = Q1 / 2;
+    static constexpr int W1 = 32 * Q1 + 4;     // level-1 box width (elements)
+    static constexpr int W2 = 32 * Q2 + 4;     // level-2 box width
+    static constexpr int R1 = round32(4 * W1);  // one level-1 box region (4 rows), 128-B multiple
+    static constexpr int R2 = round32(2 * W2);  // one level-2 box region (2 rows)
+    // NL == 1: LL1 HL1 LH1 HH1; NL == 2: HL1 LH1 HH1, LL2 HL2 LH2 HH2
+    static constexpr int SLOT = NL == 1 ? 4 * R1 : 3 * R1 + 4 * R2;
+    static constexpr uint32_t BYTES1 = 4 * W1 * sizeof(T);  // bytes one level-1 box brings
+    static constexpr uint32_t BYTES2 = 2 * W2 * sizeof(T);
+};
+
+// Lane's Q values of one band row held in shared memory at p (+ lane * Q).
+template <class T, int Q>
+__device__ __forceinline__ void lds_cols(T (&v)[Q], const T* p) {
+#pragma unroll
+    for (int j = 0; j < Q; ++j) v[j] = p[j];
+}
+
+template <class T, int SCH, int NL, int Q1>
+struct InvWarpT {
+    using Lay = InvLayout<T, NL, Q1>;
+    static constexpr int LAG = std::is_same<T, float>::value ? 2 : 1;
+    static constexpr int Q2 = Lay::Q2;
+    Engine<T, Q1, SCH, false> e1;
+    Engine<T, (Q2 > 0 ? Q2 : 1), SCH, false> e2;
+    LevelCtx x1, x2;
+    // column offsets of lane 0 inside each box (elements)
+    int o1h, o1l, o2h, o2l;
+    T* out;
+    long long opitch;
+    int out_h, out_w, xb, lane, A0, A1;
+    bool lane_ok, vec_out;
+
+    template <bool EDGE>
+    __device__ __forceinline__ void slot(const T* sm, int q0, bool level1) {
+        Block<T, Q1, 4> b1;
+        if constexpr (NL == 2) {
+            constexpr int QQ = Q2;
+            Block<T, QQ, 2> b2;
+            const T* base2 = sm + 3 * Lay::R1;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                lds_cols<T, QQ>(b2.r[k].c[0], base2 + 0 * Lay::R2 + k * Lay::W2 + o2l + QQ * lane);
+                lds_cols<T, QQ>(b2.r[k].c[1], base2 + 1 * Lay::R2 + k * Lay::W2 + o2h + QQ * lane);
+                lds_cols<T, QQ>(b2.r[k].c[2], base2 + 2 * Lay::R2 + k * Lay::W2 + o2l + QQ * lane);
+                lds_cols<T, QQ>(b2.r[k].c[3], base2 + 3 * Lay::R2 + k * Lay::W2 + o2h + QQ * lane);
+            }
+            e2.template push<EDGE, 2>(b2, q0 / 2 + LAG, x2);
+            if (!level1) return;
+            // level-2 rows q0/2, q0/2 + 1 -> LL rows q0 .. q0 + 3 of level 1
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+#pragma unroll
+                for (int j = 0; j < QQ; ++j) {
+                    b1.r[2 * k].c[0][2 * j] = b2.r[k].c[0][j];
+                    b1.r[2 * k].c[0][2 * j + 1] = b2.r[k].c[1][j];
+                    b1.r[2 * k + 1].c[0][2 * j] = b2.r[k].c[2][j];
+                    b1.r[2 * k + 1].c[0][2 * j + 1] = b2.r[k].c[3][j];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                lds_cols<T, Q1>(b1.r[k].c[1], sm + 0 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
+                lds_cols<T, Q1>(b1.r[k].c[2], sm + 1 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
+                lds_cols<T, Q1>(b1.r[k].c[3], sm + 2 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                lds_cols<T, Q1>(b1.r[k].c[0], sm + 0 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
+                lds_cols<T, Q1>(b1.r[k].c[1], sm + 1 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
+                lds_cols<T, Q1>(b1.r[k].c[2], sm + 2 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
+                lds_cols<T, Q1>(b1.r[k].c[3], sm + 3 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
+            }
+        }
+        e1.template push<EDGE, 4>(b1, q0, x1);
+        const int r1 = q0 - LAG;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) store_quad_row(b1.r[k], r1 + k);
+    }
+
+    // Quadruple row r -> output rows 2r (c0 c1 interleaved) and 2r + 1 (c2 c3).
+    __device__ __forceinline__ void store_quad_row(const Quads<T, Q1>& a, int r) {
+        if (!lane_ok || r < A0 || r >= A1) return;
+        T ev[2 * Q1], od[2 * Q1];
+#pragma unroll
+        for (int j = 0; j < Q1; ++j) {
+            ev[2 * j] = a.c[0][j];
+            ev[2 * j + 1] = a.c[1][j];
+            od[2 * j] = a.c[2][j];
+            od[2 * j + 1] = a.c[3][j];
+        }
+        store_px(ev, 2 * r);
+        store_px(od, 2 * r + 1);
+    }
+
+    __device__ __forceinline__ void store_px(const T (&v)[2 * Q1], int y) {
+        if (y >= out_h) return;
+        const int x0 = xb + 2 * Q1 * lane;
+        T* p = out + (long long)y * opitch + x0;
+        if (vec_out && x0 + 2 * Q1 <= out_w) {
+            using V = typename VecOf<T, 4>::type;
+#pragma unroll
+            for (int i = 0; i < Q1 / 2; ++i) {
+                V w;
+                T* wp = reinterpret_cast<T*>(&w);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) wp[j] = v[4 * i + j];
+                reinterpret_cast<V*>(p)[i] = w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 2 * Q1; ++j)
+                if (x0 + j >= 0 && x0 + j < out_w) p[j] = v[j];
+        }
+    }
+};
+
+__device__ __forceinline__ bool inv_rows_interior(int q0, int nl, int lag, const int* no_r) {
+    // level 1: rows [q0, q0 + 3]; level 2: rows [q0/2 + lag, q0/2 + lag + 1]
+    if (q0 - lag - 1 < 0 || q0 + 4 >= no_r[0]) return false;
+    if (nl >= 2) {
+        const int lo = q0 / 2 + lag;
+        if (lo - lag - 1 < 0 || lo + 2 >= no_r[1]) return false;
+    }
+    return true;
+}
+
+template <class T, int SCH, int NL, int Q1>
+__global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
+    inv_tma_kernel(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2,
+                   const __grid_constant__ CUtensorMap ml, const FusedArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    using W = InvWarpT<T, SCH, NL, Q1>;
+    using Lay = InvLayout<T, NL, Q1>;
+    constexpr int LAG = W::LAG;
+    constexpr int RHO = LAG;
+    constexpr int PRO = NL == 2 ? 2 * LAG : 0;  // level-2 rows pushed ahead (LAG + RHO)
+    constexpr int PRO_SLOTS = PRO / 2;           // slots that feed level 2 only
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wid = blockIdx.x * kInvWarps + warp;
+    if (wid >= a.nstrips * a.nsegs) return;
+
+    T* ring = reinterpret_cast<T*>(smem_raw) + (size_t)warp * kInvSlots * Lay::SLOT;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kInvWarps * kInvSlots *
+                                                              Lay::SLOT * sizeof(T)) +
+                     warp * kInvSlots;
+
+    const int strip = wid % a.nstrips;
+    const int seg = wid / a.nstrips;
+    W w;
+    w.lane = lane;
+    w.xb = strip * a.valid_px - a.xoff;
+    w.lane_ok = lane >= a.lane_lo && lane < a.lane_hi;
+    w.out = reinterpret_cast<T*>(a.out);
+    w.opitch = a.out_pitch;
+    w.out_h = a.lv[0].h;
+    w.out_w = a.lv[0].w;
+    w.vec_out = (a.out_pitch % 4) == 0;
+    const int ne1 = (a.lv[0].h + 1) >> 1;
+    w.A0 = seg * a.segq;
+    w.A1 = min(w.A0 + a.segq, ne1);
+
+    int no_r[2] = {a.lv[0].h >> 1, NL >= 2 ? (a.lv[1].h >> 1) : 0};
+    const int g1w = w.xb >> 1;
+    const int ne_c1 = (a.lv[0].w + 1) >> 1, ne_r1 = ne1;
+    w.x1 = make_ctx(g1w + Q1 * lane, Q1, a.lv[0].h, a.lv[0].w, a.lane_lo, a.lane_hi, a.lv[0].s);
+    const int xh1 = ne_c1 + g1w, xl1 = g1w;
+    const int bx1h = xh1 & ~3, bx1l = xl1 & ~3;
+    w.o1h = xh1 - bx1h;
+    w.o1l = xl1 - bx1l;
+    bool hfast = g1w >= 2 && g1w + 32 * Q1 + 2 <= (a.lv[0].w >> 1);
+    int bx2h = 0, bx2l = 0, ne_r2 = 0;
+    if constexpr (NL >= 2) {
+        const int g2w = w.xb >> 2;
+        const int ne_c2 = (a.lv[1].w + 1) >> 1;
+        ne_r2 = (a.lv[1].h + 1) >> 1;
+        w.x2 = make_ctx(g2w + W::Q2 * lane, W::Q2, a.lv[1].h, a.lv[1].w, a.lane_lo, a.lane_hi, a.lv[1].s);
+        const int xh2 = ne_c2 + g2w, xl2 = g2w;
+        bx2h = xh2 & ~3;
+        bx2l = xl2 & ~3;
+        w.o2h = xh2 - bx2h;
+        w.o2l = xl2 - bx2l;
+        hfast = hfast && g2w >= 2 && g2w + 32 * W::Q2 + 2 <= (a.lv[1].w >> 1);
+    }
+    w.e1.init();
+    if constexpr (NL >= 2) w.e2.init();
+
+    // level-1 input rows of this item: outputs [A0, A1) need [A0 - RHO, A1 - 1 + LAG]
+    const int qstart = max(w.A0 - RHO, 0) & ~3;
+    const int nmain = (w.A1 + LAG - qstart + 3) / 4;
+    const int nslots = nmain + PRO_SLOTS;
+    const int qbase = qstart - 4 * PRO_SLOTS;
+
+    const uint32_t ring_s = smem_u32(ring);
+    const uint32_t bar_s = smem_u32(bars);
+    auto issue = [&](int s) {
+        const int b = s % kInvSlots;
+        const uint32_t dst = ring_s + (uint32_t)(b * Lay::SLOT * sizeof(T));
+        const uint32_t bar = bar_s + 8 * b;
+        const int q0 = qbase + 4 * s;
+        const bool l1 = s >= PRO_SLOTS;
+        uint32_t bytes = 0;
+        if (l1) bytes += (NL == 1 ? 4 : 3) * Lay::BYTES1;
+        if (NL == 2) bytes += 4 * Lay::BYTES2;
+        mbar_arrive_expect_tx(bar, bytes);
+        if constexpr (NL == 1) {
+            tma_load_2d(dst + 0 * Lay::R1 * sizeof(T), &ml, bx1l, q0, bar);
+            tma_load_2d(dst + 1 * Lay::R1 * sizeof(T), &m1, bx1h, q0, bar);
+            tma_load_2d(dst + 2 * Lay::R1 * sizeof(T), &m1, bx1l, ne_r1 + q0, bar);
+            tma_load_2d(dst + 3 * Lay::R1 * sizeof(T), &m1, bx1h, ne_r1 + q0, bar);
+        } else {
+            if (l1) {
+                tma_load_2d(dst + 0 * Lay::R1 * sizeof(T), &m1, bx1h, q0, bar);
+                tma_load_2d(dst + 1 * Lay::R1 * sizeof(T), &m1, bx1l, ne_r1 + q0, bar);
+                tma_load_2d(dst + 2 * Lay::R1 * sizeof(T), &m1, bx1h, ne_r1 + q0, bar);
+            }
+            const uint32_t d2 = dst + 3 * Lay::R1 * sizeof(T);
+            const int y2 = q0 / 2 + LAG;
+            tma_load_2d(d2 + 0 * Lay::R2 * sizeof(T), &ml, bx2l, y2, bar);
+            tma_load_2d(d2 + 1 * Lay::R2 * sizeof(T), &m2, bx2h, y2, bar);
+            tma_load_2d(d2 + 2 * Lay::R2 * sizeof(T), &m2, bx2l, ne_r2 + y2, bar);
+            tma_load_2d(d2 + 3 * Lay::R2 * sizeof(T), &m2, bx2h, ne_r2 + y2, bar);
+        }
+    };
+    if (lane == 0) {
+        for (int b = 0; b < kInvSlots; ++b) mbar_init(bar_s + 8 * b, 1);
+        fence_mbar_init();
+        for (int s = 0; s < kInvSlots && s < nslots; ++s) issue(s);
+    }
+    __syncwarp();
+
+    bool failed = false;
+    int s = 0;
+    for (; s < nslots; ++s) {
+        const int b = s % kInvSlots;
+        const bool ok = mbar_wait_bounded(bar_s + 8 * b, (s / kInvSlots) & 1, kWaitBudget);
+        if (!__all_sync(kFull, ok)) {
+            failed = true;
+            break;
+        }
+        const int q0 = qbase + 4 * s;
+        const bool l1 = s >= PRO_SLOTS;
+        if (hfast && inv_rows_interior(q0, NL, LAG, no_r))
+            w.template slot<false>(ring + b * Lay::SLOT, q0, l1);
+        else
+            w.template slot<true>(ring + b * Lay::SLOT, q0, l1);
+        __syncwarp();
+        if (lane == 0 && s + kInvSlots < nslots) {
+            fence_proxy_async_smem();
+            issue(s + kInvSlots);
+        }
+    }
+    if (failed) {
+        if (lane == 0) atomicExch(a.err, -6);
+        for (int t = s; t < nslots && t < s + kInvSlots; ++t)
+            mbar_wait_bounded(bar_s + 8 * (t % kInvSlots), (t / kInvSlots) & 1, kWaitBudget);
+    }
+}
+
+size_t inv_tma_smem_bytes(int elem_bytes, int nl, int q1) {
+    const int W1 = 32 * q1 + 4, W2 = 32 * (q1 / 2) + 4;
+    const int R1 = round32(4 * W1), R2 = round32(2 * W2);
+    const int slot = nl == 1 ? 4 * R1 : 3 * R1 + 4 * R2;
+    return (size_t)kInvWarps * kInvSlots * slot * elem_bytes + (size_t)kInvWarps * kInvSlots * 8;
+}
+
+void inv_tma_boxes(int nl, int q1, int* box1, int* box2) {
+    *box1 = 32 * q1 + 4;
+    *box2 = 32 * (q1 / 2) + 4;
+    (void)nl;
+}
+
+template <class T, int SCH, int NL, int Q1>
+static cudaError_t inv_launch_one(const CUtensorMap& m1, const CUtensorMap& m2,
+                                  const CUtensorMap& ml, const FusedArgs& a, int grid,
+                                  cudaStream_t st) {
+    auto k = inv_tma_kernel<T, SCH, NL, Q1>;
+    const size_t smem = inv_tma_smem_bytes(sizeof(T), NL, Q1);
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k<<<grid, kInvWarps * 32, smem, st>>>(m1, m2, ml, a);
+    return cudaGetLastError();
+}
+
+template <class T, int SCH>
+static cudaError_t inv_launch_nl(int nl, int q1, const CUtensorMap& m1, const CUtensorMap& m2,
+                                 const CUtensorMap& ml, const FusedArgs& a, int grid,
+                                 cudaStream_t st) {
+    if (q1 == 2) {
+        if (nl == 1) return inv_launch_one<T, SCH, 1, 2>(m1, m2, ml, a, grid, st);
+        if (nl == 2) return inv_launch_one<T, SCH, 2, 2>(m1, m2, ml, a, grid, st);
+    } else if (q1 == 4) {
+        if (nl == 1) return inv_launch_one<T, SCH, 1, 4>(m1, m2, ml, a, grid, st);
+        if (nl == 2) return inv_launch_one<T, SCH, 2, 4>(m1, m2, ml, a, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class T>
+static cudaError_t inv_launch_sch(int sch, int nl, int q1, const CUtensorMap& m1,
+                                  const CUtensorMap& m2, const CUtensorMap& ml, const FusedArgs& a,
+                                  int grid, cudaStream_t st) {
+    switch (sch) {
+        case SCH_SEP: return inv_launch_nl<T, SCH_SEP>(nl, q1, m1, m2, ml, a, grid, st);
+        case SCH_NONSEP: return inv_launch_nl<T, SCH_NONSEP>(nl, q1, m1, m2, ml, a, grid, st);
+        case SCH_RED: return inv_launch_nl<T, SCH_RED>(nl, q1, m1, m2, ml, a, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_inv_tma(int elem, int scheme, int nl, int q1, const CUtensorMap& m1,
+                           const CUtensorMap& m2, const CUtensorMap& ml, const FusedArgs& a,
+                           int grid, cudaStream_t st) {
+    if (elem == 0) return inv_launch_sch<float>(scheme, nl, q1, m1, m2, ml, a, grid, st);
+    return inv_launch_sch<int>(scheme, nl, q1, m1, m2, ml, a, grid, st);
+}
+
+}  // namespace dwt
