@@ -427,8 +427,9 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
         w = (w + 1) / 2;
     }
     // level groups: the first launch fuses DWT2D_FUSE_FIRST levels (default 2),
-    // later launches up to DWT2D_FUSE (default 3) each
-    int maxf = env_int("DWT2D_FUSE", 3);
+    // later launches up to DWT2D_FUSE (default 2; 3 needs 4 columns per lane,
+    // which measured slower) each
+    int maxf = env_int("DWT2D_FUSE", 2);
     if (maxf < 1) maxf = 1;
     if (maxf > kMaxFused) maxf = kMaxFused;
     int first = env_int("DWT2D_FUSE_FIRST", maxf < 2 ? maxf : 2);
