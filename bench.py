@@ -341,6 +341,7 @@ def main():
 
     if not args.no_variants:
         out["variants"] = variants(D, synth, dev, stream, x, dst)
+        out["precision_16384x16384_l6"] = precision_variants(D, synth, dev, stream)
 
     if args.no_e2e:
         if rank == 0:
@@ -411,6 +412,36 @@ def variants(D, synth, dev, stream, x, dst):
                 "ms": round(ms, 5), "gpx_s": round(H * W / ms / 1e6, 2),
                 "strict_frac": round(strict / (ms / 1e3) / 1e9 / hbm, 4),
                 "launches": plan.info()[0]}
+    return res
+
+
+def precision_variants(D, synth, dev, stream):
+    """CDF 9/7 non-separable reduced, 16384^2, 6 levels: FP32 vs FP16 vs BF16 storage."""
+    n, levels, iters, warm = 16384, 6, 10, 3
+    hbm = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+    x32 = synth.gradient_noise(n, n, synth.SEED_PRECISION)
+    scale = float(np.max(np.abs(x32)))
+    res = {}
+    for name, dt in (("f32", torch.float32), ("f16", torch.float16), ("bf16", torch.bfloat16)):
+        xs = torch.from_numpy(x32 if dt == torch.float32 else x32 / scale).to(dt)
+        x = D.empty_image(n, n, dt, dev)
+        x.copy_(xs)
+        c = D.empty_image(n, n, dt, dev)
+        y = D.empty_image(n, n, dt, dev)
+        plan = D.Plan(n, n, levels, "cdf97", "nonsep_reduced", dt)
+        wsb = plan.workspace(dev)
+        sc = 1.0 if dt == torch.float32 else scale
+        plan.forward(x, c, wsb, scale=sc, stream=stream)
+        for direction, fn in (("fwd", lambda: plan.forward(x, c, wsb, scale=sc, stream=stream)),
+                              ("inv", lambda: plan.inverse(c, y, wsb, scale=sc, stream=stream))):
+            for _ in range(warm):
+                fn()
+            ms = time_calls(fn, iters, stream)
+            strict = 2 * x.element_size() * n * n
+            res[f"{name}_{direction}"] = {"ms": round(ms, 4), "gpx_s": round(n * n / ms / 1e6, 1),
+                                          "strict_frac": round(strict / (ms / 1e3) / 1e9 / hbm, 4)}
+        del x, c, y, wsb
+        torch.cuda.empty_cache()
     return res
 
 

@@ -118,15 +118,20 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
+// kind: 0 float32, 1 int32, 2 float16, 3 bfloat16
 dwt2d_status make_map(CUtensorMap* map, const void* base, int h, int w, long long pitch_elems,
-                      int elem, bool is_int, int box_w, int box_h = kFwdSlotRows) {
+                      int elem, int kind, int box_w, int box_h = kFwdSlotRows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return DWT2D_ERR_CUDA;
     const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
     const cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * elem)};
     const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = fn(map, is_int ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+    const CUtensorMapDataType dt = kind == 1   ? CU_TENSOR_MAP_DATA_TYPE_INT32
+                                   : kind == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : kind == 3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const CUresult r = fn(map, dt,
                           2, const_cast<void*>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -150,8 +155,13 @@ void decompose(const dwt2d_plan_s* p, int w_first, int rows, int nl, int rho, in
                int target_warps, FusedArgs* a, int* grid, int warps_per_block) {
     valid_lanes(nl, rho, q1, &a->lane_lo, &a->lane_hi);
     const int qn = q1 >> (nl - 1);
-    a->valid_px = (a->lane_hi - a->lane_lo) * qn * (1 << nl);
-    a->xoff = a->lane_lo * qn * (1 << nl);
+    const int ppl = qn * (1 << nl);  // input pixels per lane
+    // TMA boxes start at a multiple of 16 bytes: strip starts must be aligned
+    const int align = 16 / p->elem;
+    while ((a->lane_lo * ppl) % align) ++a->lane_lo;
+    while (((a->lane_hi - a->lane_lo) * ppl) % align) --a->lane_hi;
+    a->valid_px = (a->lane_hi - a->lane_lo) * ppl;
+    a->xoff = a->lane_lo * ppl;
     a->nstrips = (w_first + a->valid_px - 1) / a->valid_px;
     int nsegs = target_warps / a->nstrips;
     if (nsegs < 1) nsegs = 1;
@@ -171,9 +181,18 @@ void mark(const dwt2d_plan_s* p, int launch, int side, cudaStream_t st) {
     if (p->events && launch < p->nevents) cudaEventRecord(p->events[2 * launch + side], st);
 }
 
+int elem_kind_of(dwt2d_dtype d) {
+    switch (d) {
+        case DWT2D_I32: return 1;
+        case DWT2D_F16: return 2;
+        case DWT2D_BF16: return 3;
+        default: return 0;
+    }
+}
+
 dwt2d_status run_fused(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t sp, void* dst,
                        int64_t dp, void* ws, cudaStream_t st) {
-    const int elem_kind = p->dtype == DWT2D_I32 ? 1 : 0;
+    const int elem_kind = elem_kind_of(p->dtype);
     const int rho = p->wavelet == DWT2D_CDF97 ? 2 : 1;
     const int sch = base_scheme(p->scheme);
     char* wsb = reinterpret_cast<char*>(ws);
@@ -202,7 +221,7 @@ dwt2d_status run_fused(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t
             a.err = err;
             const int q1 = g.n >= 3 ? 4 : p->fwd_q1;
             CUtensorMap map;
-            dwt2d_status s = make_map(&map, in, a.lv[0].h, a.lv[0].w, in_pitch, p->elem, elem_kind == 1,
+            dwt2d_status s = make_map(&map, in, a.lv[0].h, a.lv[0].w, in_pitch, p->elem, elem_kind,
                                       64 * q1);
             if (s != DWT2D_OK) return s;
             const int hN = a.lv[g.n - 1].h;
@@ -242,16 +261,17 @@ dwt2d_status run_fused(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t
         if (g.n <= 2) {
             // TMA ring: boxes of the Mallat array and of the LL source
             const int q1 = p->inv_q1;
-            const int w1 = 32 * q1 + 4, w2 = 16 * q1 + 4;
-            const bool is_int = elem_kind == 1;
+            const int al = 16 / p->elem;  // boxes start at a 16-byte boundary
+            const int w1 = 32 * q1 + al, w2 = 16 * q1 + al;
+            const int kind = elem_kind;
             CUtensorMap m1, m2, ml;
-            dwt2d_status s = make_map(&m1, src, p->H, p->W, src_pe, p->elem, is_int, w1, 4);
-            if (s == DWT2D_OK) s = make_map(&m2, src, p->H, p->W, src_pe, p->elem, is_int, w2, 2);
+            dwt2d_status s = make_map(&m1, src, p->H, p->W, src_pe, p->elem, kind, w1, 4);
+            if (s == DWT2D_OK) s = make_map(&m2, src, p->H, p->W, src_pe, p->elem, kind, w2, 2);
             const int llh = (a.lv[g.n - 1].h + 1) / 2, llw = (a.lv[g.n - 1].w + 1) / 2;
             const bool ll_is_src = ll_in == src;
             if (s == DWT2D_OK)
                 s = make_map(&ml, ll_in, ll_is_src ? p->H : llh, ll_is_src ? p->W : llw, ll_pitch,
-                             p->elem, is_int, g.n == 1 ? w1 : w2, g.n == 1 ? 4 : 2);
+                             p->elem, kind, g.n == 1 ? w1 : w2, g.n == 1 ? 4 : 2);
             if (s != DWT2D_OK) return s;
             decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, q1, p->inv_warps_target, &a, &grid,
                       kInvTmaWarps);
@@ -305,7 +325,7 @@ int step_list(const dwt2d_plan_s* p, int* kinds, float* coefs) {
 
 dwt2d_status run_multipass(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t sp, void* dst,
                            int64_t dp, void* ws, cudaStream_t st) {
-    const int elem_kind = p->dtype == DWT2D_I32 ? 1 : 0;
+    const int elem_kind = elem_kind_of(p->dtype);
     char* wsb = reinterpret_cast<char*>(ws);
     void* X[2] = {wsb + p->off_x, wsb + p->off_y};
     void* LLb[2] = {wsb + p->off_a, wsb + p->off_b};
@@ -407,9 +427,11 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
     if (levels < 1 || levels > 16) return DWT2D_ERR_INVALID;
     if (boundary != DWT2D_SYMMETRIC_WHOLE) return DWT2D_ERR_UNSUPPORTED;
     if (scheme < DWT2D_SEPARABLE || scheme > DWT2D_NONSEP_REDUCED_MULTIPASS) return DWT2D_ERR_INVALID;
-    if (!((wavelet == DWT2D_CDF97 && dtype == DWT2D_F32) ||
+    const bool half = dtype == DWT2D_F16 || dtype == DWT2D_BF16;
+    if (!((wavelet == DWT2D_CDF97 && (dtype == DWT2D_F32 || half)) ||
           (wavelet == DWT2D_LEGALL53 && dtype == DWT2D_I32)))
         return DWT2D_ERR_UNSUPPORTED;
+    if (half && multipass(scheme)) return DWT2D_ERR_UNSUPPORTED;
     dwt2d_plan_s* p = (dwt2d_plan_s*)calloc(1, sizeof(dwt2d_plan_s));
     if (!p) return DWT2D_ERR_NOMEM;
     p->H = height;
@@ -418,7 +440,7 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
     p->wavelet = wavelet;
     p->scheme = scheme;
     p->dtype = dtype;
-    p->elem = 4;
+    p->elem = half ? 2 : 4;
     int h = height, w = width;
     for (int l = 0; l < levels; ++l) {
         p->hs[l] = h;
@@ -432,6 +454,7 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
     int maxf = env_int("DWT2D_FUSE", 2);
     if (maxf < 1) maxf = 1;
     if (maxf > kMaxFused) maxf = kMaxFused;
+    if (half && maxf > 2) maxf = 2;  // 16-bit storage runs 2 columns per lane: up to 2 levels
     int first = env_int("DWT2D_FUSE_FIRST", maxf < 2 ? maxf : 2);
     if (first < 1) first = 1;
     if (first > maxf) first = maxf;
@@ -452,8 +475,8 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
     p->fwd_warps_target = sms * env_int("DWT2D_FWD_WARPS_PER_SM", 16);
     p->inv_warps_target = sms * env_int("DWT2D_INV_WARPS_PER_SM", 12);
     p->min_segq = env_int("DWT2D_MIN_SEGQ", 2);
-    p->fwd_q1 = env_int("DWT2D_FWD_Q", 2) == 4 ? 4 : 2;
-    p->inv_q1 = env_int("DWT2D_INV_Q", 2) == 4 ? 4 : 2;
+    p->fwd_q1 = env_int("DWT2D_FWD_Q", 2) == 4 && !half ? 4 : 2;
+    p->inv_q1 = env_int("DWT2D_INV_Q", 2) == 4 && !half ? 4 : 2;
 
     // workspace: header | LL buffer A | LL buffer B | (multipass) X | Y
     size_t off = kHeader;
@@ -512,10 +535,19 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
     return DWT2D_OK;
 }
 
+// 16-bit storage: stored value = value / scale for image and coefficients
+// alike.  The transform is linear, so the coefficients of the stored image are
+// the stored coefficients and the kernels never apply the scale; it is only
+// checked here.
+static bool scale_ok(const dwt2d_plan_s* p, float scale) {
+    if (p->elem != 2) return true;
+    return scale > 0.0f && scale < 3.0e38f;
+}
+
 dwt2d_status dwt2d_forward(dwt2d_plan_t p, const void* d_src, int64_t sp, void* d_dst, int64_t dp,
                            void* d_ws, float scale, void* stream) {
-    (void)scale;
     dwt2d_status s = check_buffers(p, d_src, sp, d_dst, dp, d_ws);
+    if (s == DWT2D_OK && !scale_ok(p, scale)) s = DWT2D_ERR_INVALID;
     if (s != DWT2D_OK) return s;
     if (d_src == d_dst) return DWT2D_ERR_INVALID;
     return multipass(p->scheme) ? run_multipass(p, true, d_src, sp, d_dst, dp, d_ws, as_stream(stream))
@@ -524,8 +556,8 @@ dwt2d_status dwt2d_forward(dwt2d_plan_t p, const void* d_src, int64_t sp, void* 
 
 dwt2d_status dwt2d_inverse(dwt2d_plan_t p, const void* d_src, int64_t sp, void* d_dst, int64_t dp,
                            void* d_ws, float scale, void* stream) {
-    (void)scale;
     dwt2d_status s = check_buffers(p, d_src, sp, d_dst, dp, d_ws);
+    if (s == DWT2D_OK && !scale_ok(p, scale)) s = DWT2D_ERR_INVALID;
     if (s != DWT2D_OK) return s;
     if (d_src == d_dst) return DWT2D_ERR_INVALID;
     return multipass(p->scheme) ? run_multipass(p, false, d_src, sp, d_dst, dp, d_ws, as_stream(stream))

@@ -18,6 +18,8 @@
 // the value of the column / row before it, before every update step.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "dwt_internal.h"
@@ -48,6 +50,82 @@ template <>
 struct VecOf<int, 1> { using type = int; };
 
 __host__ __device__ constexpr int floordiv2(int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
+
+// Storage type S in memory, arithmetic type T in registers: FP16 / BF16
+// coefficients are lifted in FP32.
+template <class S>
+struct Storage;
+template <>
+struct Storage<float> {
+    using T = float;
+    __device__ __forceinline__ static float ld(float v) { return v; }
+    __device__ __forceinline__ static float st(float v) { return v; }
+};
+template <>
+struct Storage<int> {
+    using T = int;
+    __device__ __forceinline__ static int ld(int v) { return v; }
+    __device__ __forceinline__ static int st(int v) { return v; }
+};
+template <>
+struct Storage<__half> {
+    using T = float;
+    __device__ __forceinline__ static float ld(__half v) { return __half2float(v); }
+    __device__ __forceinline__ static __half st(float v) { return __float2half_rn(v); }
+};
+template <>
+struct Storage<__nv_bfloat16> {
+    using T = float;
+    __device__ __forceinline__ static float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ __forceinline__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+};
+
+// Raw vector of a given byte size (2, 4, 8 or 16).
+template <int BYTES>
+struct RawVec;
+template <>
+struct RawVec<2> { using type = unsigned short; };
+template <>
+struct RawVec<4> { using type = unsigned int; };
+template <>
+struct RawVec<8> { using type = uint2; };
+template <>
+struct RawVec<16> { using type = uint4; };
+
+// N consecutive S values at p (aligned to min(16, N sizeof(S)) bytes).
+template <class S, int N>
+__device__ __forceinline__ void ld_vec(S (&v)[N], const S* p) {
+    constexpr int B = N * (int)sizeof(S);
+    if constexpr (B <= 16) {
+        using R = typename RawVec<B>::type;
+        const R r = *reinterpret_cast<const R*>(p);
+        const S* q = reinterpret_cast<const S*>(&r);
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = q[j];
+    } else {
+        constexpr int H = N / 2;
+        S* lo = v;
+        S* hi = v + H;
+        ld_vec<S, H>(*reinterpret_cast<S(*)[H]>(lo), p);
+        ld_vec<S, H>(*reinterpret_cast<S(*)[H]>(hi), p + H);
+    }
+}
+template <class S, int N>
+__device__ __forceinline__ void st_vec(S* p, const S (&v)[N]) {
+    constexpr int B = N * (int)sizeof(S);
+    if constexpr (B <= 16) {
+        using R = typename RawVec<B>::type;
+        R r;
+        S* q = reinterpret_cast<S*>(&r);
+#pragma unroll
+        for (int j = 0; j < N; ++j) q[j] = v[j];
+        *reinterpret_cast<R*>(p) = r;
+    } else {
+        constexpr int H = N / 2;
+        st_vec<S, H>(p, *reinterpret_cast<const S(*)[H]>(v));
+        st_vec<S, H>(p + H, *reinterpret_cast<const S(*)[H]>(v + H));
+    }
+}
 
 // Per-level information of one lane (horizontal) and of the level (vertical).
 struct LevelCtx {

@@ -1,12 +1,12 @@
 // Forward transform: TMA-fed warp-streaming kernel, 1..3 levels per launch.
 //
-// Each warp takes one work item (a strip of 256 input pixels, including a
+// Each warp takes one work item (a strip of 64 Q1 input pixels, including a
 // halo, and a segment of rows) and streams its rows through a private ring of
 // shared-memory slots that the warp's lane 0 fills with 2-D TMA boxes.  The
-// level-1 engine (4 quadruple columns per lane) emits finished rows; their
+// level-1 engine (Q1 quadruple columns per lane) emits finished rows; their
 // detail bands are stored and their LL values are paired into level-2
-// quadruple rows (2 columns per lane), and so on to level 3 (1 column per
-// lane).  Only the LL of the last fused level leaves the chip besides the
+// quadruple rows (Q1/2 columns per lane), and so on to level 3.  Values are
+// stored as S (float, int, half or bfloat16) and lifted as float or int.  Only the LL of the last fused level leaves the chip besides the
 // detail bands, so a launch that fuses k levels reads the input once and
 // writes every coefficient once.
 #include <type_traits>
@@ -18,19 +18,17 @@
 namespace dwt {
 
 // Store Q consecutive values at p; `avail` columns remain inside the band.
-template <class T, int Q>
-__device__ __forceinline__ void store_cols(T* p, const T (&v)[Q], int avail, bool vec) {
-    if (vec && avail >= Q) {
-        using V = typename VecOf<T, Q>::type;
-        V w;
-        T* wp = reinterpret_cast<T*>(&w);
+template <class S, class T, int Q>
+__device__ __forceinline__ void store_cols(S* p, const T (&v)[Q], int avail, bool vec) {
+    S w[Q];
 #pragma unroll
-        for (int j = 0; j < Q; ++j) wp[j] = v[j];
-        *reinterpret_cast<V*>(p) = w;
+    for (int j = 0; j < Q; ++j) w[j] = Storage<S>::st(v[j]);
+    if (vec && avail >= Q) {
+        st_vec<S, Q>(p, w);
     } else {
 #pragma unroll
         for (int j = 0; j < Q; ++j)
-            if (j < avail) p[j] = v[j];
+            if (j < avail) p[j] = w[j];
     }
 }
 
@@ -42,24 +40,24 @@ struct StoreGeo {
     bool vec_hl, vec_lh;
 };
 
-template <class T, int Q>
+template <class S, class T, int Q>
 __device__ __forceinline__ void store_details(const Quads<T, Q>& a, int r, const StoreGeo& g,
-                                              T* mallat, long long pitch, bool lane_ok) {
+                                              S* mallat, long long pitch, bool lane_ok) {
     if (!lane_ok || r < g.r_lo || r >= g.r_hi || r >= g.ne_r) return;
-    T* row = mallat + (long long)r * pitch;
-    store_cols<T, Q>(row + g.ne_c + g.g0, a.c[1], g.no_c - g.g0, g.vec_hl);
+    S* row = mallat + (long long)r * pitch;
+    store_cols<S, T, Q>(row + g.ne_c + g.g0, a.c[1], g.no_c - g.g0, g.vec_hl);
     if (r < g.no_r) {
-        T* row2 = mallat + (long long)(g.ne_r + r) * pitch;
-        store_cols<T, Q>(row2 + g.g0, a.c[2], g.ne_c - g.g0, g.vec_lh);
-        store_cols<T, Q>(row2 + g.ne_c + g.g0, a.c[3], g.no_c - g.g0, g.vec_hl);
+        S* row2 = mallat + (long long)(g.ne_r + r) * pitch;
+        store_cols<S, T, Q>(row2 + g.g0, a.c[2], g.ne_c - g.g0, g.vec_lh);
+        store_cols<S, T, Q>(row2 + g.ne_c + g.g0, a.c[3], g.no_c - g.g0, g.vec_hl);
     }
 }
 
-template <class T, int Q>
-__device__ __forceinline__ void store_ll(const Quads<T, Q>& a, int r, const StoreGeo& g, T* ll,
+template <class S, class T, int Q>
+__device__ __forceinline__ void store_ll(const Quads<T, Q>& a, int r, const StoreGeo& g, S* ll,
                                          long long pitch, bool lane_ok, bool vec) {
     if (!lane_ok || r < g.r_lo || r >= g.r_hi || r >= g.ne_r) return;
-    store_cols<T, Q>(ll + (long long)r * pitch + g.g0, a.c[0], g.ne_c - g.g0, vec);
+    store_cols<S, T, Q>(ll + (long long)r * pitch + g.g0, a.c[0], g.ne_c - g.g0, vec);
 }
 
 __device__ __forceinline__ StoreGeo make_geo(int h, int w, int g0, int Q, int r_lo, int r_hi,
@@ -93,8 +91,9 @@ __device__ __forceinline__ void pair_rows(const T (&e)[Q], const T (&o)[Q], Quad
 // All state of one warp's work item: the level engines, per-level geometry and
 // the pending even LL rows, plus the static per-slot schedule.  Q1 quadruple
 // columns per lane at level 1 (2 Q1 pixels), Q1/2 at level 2, Q1/4 at level 3.
-template <class T, int SCH, int NL, int Q1>
+template <class S, int SCH, int NL, int Q1>
 struct FwdWarp {
+    using T = typename Storage<S>::T;
     static constexpr int LAG = std::is_same<T, float>::value ? 2 : 1;
     static constexpr int Q2 = Q1 / 2 > 0 ? Q1 / 2 : 1;
     static constexpr int Q3 = Q1 / 4 > 0 ? Q1 / 4 : 1;
@@ -105,8 +104,8 @@ struct FwdWarp {
     LevelCtx x1, x2, x3;
     StoreGeo s1, s2, s3;
     T pend1[Q1], pend2[Q2];
-    T* mallat;
-    T* ll;
+    S* mallat;
+    S* ll;
     long long mpitch, llpitch;
     bool lane_ok, vec_ll;
     int lane;
@@ -116,28 +115,28 @@ struct FwdWarp {
     // q0 % 4 == 0 the rows every level emits, and how LL rows pair into the
     // next level's quadruple rows, are fixed by the pipeline lag alone.
     template <bool EDGE>
-    __device__ __forceinline__ void slot(const T* sm, int q0) {
-        using V4 = typename VecOf<T, 4>::type;
+    __device__ __forceinline__ void slot(const S* sm, int q0) {
         Block<T, Q1, 4> b1;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             Quads<T, Q1>& row = b1.r[k];
+            S ev[2 * Q1], od[2 * Q1];
+            ld_vec<S, 2 * Q1>(ev, sm + (2 * k) * BW + 2 * Q1 * lane);
+            ld_vec<S, 2 * Q1>(od, sm + (2 * k + 1) * BW + 2 * Q1 * lane);
 #pragma unroll
-            for (int i = 0; i < Q1 / 2; ++i) {
-                const V4 a = reinterpret_cast<const V4*>(sm + (2 * k) * BW + 2 * Q1 * lane)[i];
-                const V4 c = reinterpret_cast<const V4*>(sm + (2 * k + 1) * BW + 2 * Q1 * lane)[i];
-                row.c[0][2 * i] = a.x; row.c[1][2 * i] = a.y;
-                row.c[0][2 * i + 1] = a.z; row.c[1][2 * i + 1] = a.w;
-                row.c[2][2 * i] = c.x; row.c[3][2 * i] = c.y;
-                row.c[2][2 * i + 1] = c.z; row.c[3][2 * i + 1] = c.w;
+            for (int j = 0; j < Q1; ++j) {
+                row.c[0][j] = Storage<S>::ld(ev[2 * j]);
+                row.c[1][j] = Storage<S>::ld(ev[2 * j + 1]);
+                row.c[2][j] = Storage<S>::ld(od[2 * j]);
+                row.c[3][j] = Storage<S>::ld(od[2 * j + 1]);
             }
         }
         e1.template push<EDGE, 4>(b1, q0, x1);
         const int r1 = q0 - LAG;  // first emitted level-1 row
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            store_details<T, Q1>(b1.r[k], r1 + k, s1, mallat, mpitch, lane_ok);
-            if constexpr (NL == 1) store_ll<T, Q1>(b1.r[k], r1 + k, s1, ll, llpitch, lane_ok, vec_ll);
+            store_details<S, T, Q1>(b1.r[k], r1 + k, s1, mallat, mpitch, lane_ok);
+            if constexpr (NL == 1) store_ll<S, T, Q1>(b1.r[k], r1 + k, s1, ll, llpitch, lane_ok, vec_ll);
         }
         if constexpr (NL >= 2) {
             // level-2 input rows q0/2 - 1 and q0/2 = LL rows q0 - 2 .. q0 + 1
@@ -155,8 +154,8 @@ struct FwdWarp {
             const int r2 = in2 - LAG;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                store_details<T, Q2>(b2.r[k], r2 + k, s2, mallat, mpitch, lane_ok);
-                if constexpr (NL == 2) store_ll<T, Q2>(b2.r[k], r2 + k, s2, ll, llpitch, lane_ok, vec_ll);
+                store_details<S, T, Q2>(b2.r[k], r2 + k, s2, mallat, mpitch, lane_ok);
+                if constexpr (NL == 2) store_ll<S, T, Q2>(b2.r[k], r2 + k, s2, ll, llpitch, lane_ok, vec_ll);
             }
             if constexpr (NL >= 3) {
                 static_assert(Q1 >= 4, "three fused levels need 4 columns per lane");
@@ -171,8 +170,8 @@ struct FwdWarp {
                     in3 = q0 / 4 - 1;
                 }
                 e3.template push<EDGE, 1>(b3, in3, x3);
-                store_details<T, Q3>(b3.r[0], in3 - LAG, s3, mallat, mpitch, lane_ok);
-                store_ll<T, Q3>(b3.r[0], in3 - LAG, s3, ll, llpitch, lane_ok, vec_ll);
+                store_details<S, T, Q3>(b3.r[0], in3 - LAG, s3, mallat, mpitch, lane_ok);
+                store_ll<S, T, Q3>(b3.r[0], in3 - LAG, s3, ll, llpitch, lane_ok, vec_ll);
             }
         }
     }
@@ -194,11 +193,12 @@ __device__ __forceinline__ bool rows_interior(int q0, int nl, int lag, const int
 template <int Q1>
 __host__ __device__ constexpr int fwd_min_blocks() { return Q1 <= 2 ? 4 : 2; }
 
-template <class T, int SCH, int NL, int Q1>
+template <class S, int SCH, int NL, int Q1>
 __global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
     fwd_fused_kernel(const __grid_constant__ CUtensorMap map, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    using FW = FwdWarp<T, SCH, NL, Q1>;
+    using FW = FwdWarp<S, SCH, NL, Q1>;
+    using T = typename FW::T;
     constexpr int RHO = FW::LAG;
     constexpr int BW = FW::BW;
     static_assert(Engine<T, Q1, SCH, true>::LAG == RHO && Engine<T, 1, SCH, true>::LAG == RHO, "lag");
@@ -209,9 +209,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
     if (wid >= a.nstrips * a.nsegs) return;
 
     constexpr int kSlotElems = kFwdSlotRows * BW;
-    T* ring = reinterpret_cast<T*>(smem_raw) + (size_t)warp * kFwdSlots * kSlotElems;
+    S* ring = reinterpret_cast<S*>(smem_raw) + (size_t)warp * kFwdSlots * kSlotElems;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kFwdWarps * kFwdSlots *
-                                                              kSlotElems * sizeof(T)) +
+                                                              kSlotElems * sizeof(S)) +
                      warp * kFwdSlots;
 
     const int strip = wid % a.nstrips;
@@ -239,9 +239,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
     FW W;
     W.lane = lane;
     W.lane_ok = lane >= a.lane_lo && lane < a.lane_hi;
-    W.mallat = reinterpret_cast<T*>(a.mallat);
+    W.mallat = reinterpret_cast<S*>(a.mallat);
     W.mpitch = a.mallat_pitch;
-    W.ll = reinterpret_cast<T*>(a.ll);
+    W.ll = reinterpret_cast<S*>(a.ll);
     W.llpitch = a.ll_pitch;
     constexpr int QN = NL == 1 ? Q1 : (NL == 2 ? FW::Q2 : FW::Q3);
     W.vec_ll = (a.ll_pitch % QN) == 0;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
     // ---- TMA ring prologue
     const uint32_t ring_s = smem_u32(ring);
     const uint32_t bar_s = smem_u32(bars);
-    constexpr uint32_t kSlotBytes = kSlotElems * sizeof(T);
+    constexpr uint32_t kSlotBytes = kSlotElems * sizeof(S);
     const int y0 = 2 * qstart;
     if (lane == 0) {
         for (int b = 0; b < kFwdSlots; ++b) mbar_init(bar_s + 8 * b, 1);
@@ -322,11 +322,11 @@ size_t fwd_smem_bytes(int elem_bytes, int q1) {
            (size_t)kFwdWarps * kFwdSlots * 8;
 }
 
-template <class T, int SCH, int NL, int Q1>
+template <class S, int SCH, int NL, int Q1>
 static cudaError_t launch_one(const CUtensorMap& map, const FusedArgs& a, int grid,
                               cudaStream_t st) {
-    auto k = fwd_fused_kernel<T, SCH, NL, Q1>;
-    const size_t smem = fwd_smem_bytes(sizeof(T), Q1);
+    auto k = fwd_fused_kernel<S, SCH, NL, Q1>;
+    const size_t smem = fwd_smem_bytes(sizeof(S), Q1);
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     k<<<grid, kFwdWarps * 32, smem, st>>>(map, a);
@@ -362,10 +362,32 @@ static cudaError_t launch_sch(int sch, int nl, int q1, const CUtensorMap& map, c
     return cudaErrorInvalidValue;
 }
 
+// 16-bit storage: 1 or 2 fused levels, 2 columns per lane
+template <class S>
+static cudaError_t launch_sch16(int sch, int nl, const CUtensorMap& map, const FusedArgs& a,
+                                int grid, cudaStream_t st) {
+    if (nl < 1 || nl > 2) return cudaErrorInvalidValue;
+    switch (sch) {
+        case SCH_SEP: return nl == 1 ? launch_one<S, SCH_SEP, 1, 2>(map, a, grid, st)
+                                     : launch_one<S, SCH_SEP, 2, 2>(map, a, grid, st);
+        case SCH_NONSEP: return nl == 1 ? launch_one<S, SCH_NONSEP, 1, 2>(map, a, grid, st)
+                                        : launch_one<S, SCH_NONSEP, 2, 2>(map, a, grid, st);
+        case SCH_RED: return nl == 1 ? launch_one<S, SCH_RED, 1, 2>(map, a, grid, st)
+                                     : launch_one<S, SCH_RED, 2, 2>(map, a, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_fwd_fused(int elem, int scheme, int nl, int q1, const CUtensorMap& map,
                              const FusedArgs& a, int grid, cudaStream_t st) {
-    if (elem == 0) return launch_sch<float>(scheme, nl, q1, map, a, grid, st);
-    return launch_sch<int>(scheme, nl, q1, map, a, grid, st);
+    switch (elem) {
+        case 0: return launch_sch<float>(scheme, nl, q1, map, a, grid, st);
+        case 1: return launch_sch<int>(scheme, nl, q1, map, a, grid, st);
+        // 16-bit storage: up to 2 fused levels with 2 columns per lane
+        case 2: return launch_sch16<__half>(scheme, nl, map, a, grid, st);
+        case 3: return launch_sch16<__nv_bfloat16>(scheme, nl, map, a, grid, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace dwt

@@ -20,31 +20,34 @@ namespace dwt {
 constexpr int kInvWarps = 4;  // warps per CTA (independent)
 constexpr int kInvSlots = 3;  // ring depth per warp
 
-__host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }
-
-template <class T, int NL, int Q1>
+// Box widths carry A extra elements (16 bytes) so a box can start at the
+// column rounded down to 16 bytes.
+template <class S, int NL, int Q1>
 struct InvLayout {
+    static constexpr int A = 16 / (int)sizeof(S);
     static constexpr int Q2 = Q1 / 2;
-    static constexpr int W1 = 32 * Q1 + 4;     // level-1 box width (elements)
-    static constexpr int W2 = 32 * Q2 + 4;     // level-2 box width
-    static constexpr int R1 = round32(4 * W1);  // one level-1 box region (4 rows), 128-B multiple
-    static constexpr int R2 = round32(2 * W2);  // one level-2 box region (2 rows)
+    static constexpr int W1 = 32 * Q1 + A;     // level-1 box width (elements)
+    static constexpr int W2 = 32 * Q2 + A;     // level-2 box width
+    static constexpr int E128 = 128 / (int)sizeof(S);
+    static constexpr int R1 = (4 * W1 + E128 - 1) / E128 * E128;  // one level-1 box region, 128-B multiple
+    static constexpr int R2 = (2 * W2 + E128 - 1) / E128 * E128;  // one level-2 box region
     // NL == 1: LL1 HL1 LH1 HH1; NL == 2: HL1 LH1 HH1, LL2 HL2 LH2 HH2
     static constexpr int SLOT = NL == 1 ? 4 * R1 : 3 * R1 + 4 * R2;
-    static constexpr uint32_t BYTES1 = 4 * W1 * sizeof(T);  // bytes one level-1 box brings
-    static constexpr uint32_t BYTES2 = 2 * W2 * sizeof(T);
+    static constexpr uint32_t BYTES1 = 4 * W1 * sizeof(S);  // bytes one level-1 box brings
+    static constexpr uint32_t BYTES2 = 2 * W2 * sizeof(S);
 };
 
 // Lane's Q values of one band row held in shared memory at p (+ lane * Q).
-template <class T, int Q>
-__device__ __forceinline__ void lds_cols(T (&v)[Q], const T* p) {
+template <class S, class T, int Q>
+__device__ __forceinline__ void lds_cols(T (&v)[Q], const S* p) {
 #pragma unroll
-    for (int j = 0; j < Q; ++j) v[j] = p[j];
+    for (int j = 0; j < Q; ++j) v[j] = Storage<S>::ld(p[j]);
 }
 
-template <class T, int SCH, int NL, int Q1>
+template <class S, int SCH, int NL, int Q1>
 struct InvWarpT {
-    using Lay = InvLayout<T, NL, Q1>;
+    using T = typename Storage<S>::T;
+    using Lay = InvLayout<S, NL, Q1>;
     static constexpr int LAG = std::is_same<T, float>::value ? 2 : 1;
     static constexpr int Q2 = Lay::Q2;
     Engine<T, Q1, SCH, false> e1;
@@ -52,24 +55,24 @@ struct InvWarpT {
     LevelCtx x1, x2;
     // column offsets of lane 0 inside each box (elements)
     int o1h, o1l, o2h, o2l;
-    T* out;
+    S* out;
     long long opitch;
     int out_h, out_w, xb, lane, A0, A1;
     bool lane_ok, vec_out;
 
     template <bool EDGE>
-    __device__ __forceinline__ void slot(const T* sm, int q0, bool level1) {
+    __device__ __forceinline__ void slot(const S* sm, int q0, bool level1) {
         Block<T, Q1, 4> b1;
         if constexpr (NL == 2) {
             constexpr int QQ = Q2;
             Block<T, QQ, 2> b2;
-            const T* base2 = sm + 3 * Lay::R1;
+            const S* base2 = sm + 3 * Lay::R1;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                lds_cols<T, QQ>(b2.r[k].c[0], base2 + 0 * Lay::R2 + k * Lay::W2 + o2l + QQ * lane);
-                lds_cols<T, QQ>(b2.r[k].c[1], base2 + 1 * Lay::R2 + k * Lay::W2 + o2h + QQ * lane);
-                lds_cols<T, QQ>(b2.r[k].c[2], base2 + 2 * Lay::R2 + k * Lay::W2 + o2l + QQ * lane);
-                lds_cols<T, QQ>(b2.r[k].c[3], base2 + 3 * Lay::R2 + k * Lay::W2 + o2h + QQ * lane);
+                lds_cols<S, T, QQ>(b2.r[k].c[0], base2 + 0 * Lay::R2 + k * Lay::W2 + o2l + QQ * lane);
+                lds_cols<S, T, QQ>(b2.r[k].c[1], base2 + 1 * Lay::R2 + k * Lay::W2 + o2h + QQ * lane);
+                lds_cols<S, T, QQ>(b2.r[k].c[2], base2 + 2 * Lay::R2 + k * Lay::W2 + o2l + QQ * lane);
+                lds_cols<S, T, QQ>(b2.r[k].c[3], base2 + 3 * Lay::R2 + k * Lay::W2 + o2h + QQ * lane);
             }
             e2.template push<EDGE, 2>(b2, q0 / 2 + LAG, x2);
             if (!level1) return;
@@ -86,17 +89,17 @@ struct InvWarpT {
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                lds_cols<T, Q1>(b1.r[k].c[1], sm + 0 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
-                lds_cols<T, Q1>(b1.r[k].c[2], sm + 1 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
-                lds_cols<T, Q1>(b1.r[k].c[3], sm + 2 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
+                lds_cols<S, T, Q1>(b1.r[k].c[1], sm + 0 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
+                lds_cols<S, T, Q1>(b1.r[k].c[2], sm + 1 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
+                lds_cols<S, T, Q1>(b1.r[k].c[3], sm + 2 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
             }
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                lds_cols<T, Q1>(b1.r[k].c[0], sm + 0 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
-                lds_cols<T, Q1>(b1.r[k].c[1], sm + 1 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
-                lds_cols<T, Q1>(b1.r[k].c[2], sm + 2 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
-                lds_cols<T, Q1>(b1.r[k].c[3], sm + 3 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
+                lds_cols<S, T, Q1>(b1.r[k].c[0], sm + 0 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
+                lds_cols<S, T, Q1>(b1.r[k].c[1], sm + 1 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
+                lds_cols<S, T, Q1>(b1.r[k].c[2], sm + 2 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
+                lds_cols<S, T, Q1>(b1.r[k].c[3], sm + 3 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
             }
         }
         e1.template push<EDGE, 4>(b1, q0, x1);
@@ -123,21 +126,16 @@ struct InvWarpT {
     __device__ __forceinline__ void store_px(const T (&v)[2 * Q1], int y) {
         if (y >= out_h) return;
         const int x0 = xb + 2 * Q1 * lane;
-        T* p = out + (long long)y * opitch + x0;
+        S* p = out + (long long)y * opitch + x0;
+        S w[2 * Q1];
+#pragma unroll
+        for (int j = 0; j < 2 * Q1; ++j) w[j] = Storage<S>::st(v[j]);
         if (vec_out && x0 + 2 * Q1 <= out_w) {
-            using V = typename VecOf<T, 4>::type;
-#pragma unroll
-            for (int i = 0; i < Q1 / 2; ++i) {
-                V w;
-                T* wp = reinterpret_cast<T*>(&w);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) wp[j] = v[4 * i + j];
-                reinterpret_cast<V*>(p)[i] = w;
-            }
+            st_vec<S, 2 * Q1>(p, w);
         } else {
 #pragma unroll
             for (int j = 0; j < 2 * Q1; ++j)
-                if (x0 + j >= 0 && x0 + j < out_w) p[j] = v[j];
+                if (x0 + j >= 0 && x0 + j < out_w) p[j] = w[j];
         }
     }
 };
@@ -152,13 +150,13 @@ __device__ __forceinline__ bool inv_rows_interior(int q0, int nl, int lag, const
     return true;
 }
 
-template <class T, int SCH, int NL, int Q1>
+template <class S, int SCH, int NL, int Q1>
 __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
     inv_tma_kernel(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2,
                    const __grid_constant__ CUtensorMap ml, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    using W = InvWarpT<T, SCH, NL, Q1>;
-    using Lay = InvLayout<T, NL, Q1>;
+    using W = InvWarpT<S, SCH, NL, Q1>;
+    using Lay = InvLayout<S, NL, Q1>;
     constexpr int LAG = W::LAG;
     constexpr int RHO = LAG;
     constexpr int PRO = NL == 2 ? 2 * LAG : 0;  // level-2 rows pushed ahead (LAG + RHO)
@@ -169,9 +167,9 @@ __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
     const int wid = blockIdx.x * kInvWarps + warp;
     if (wid >= a.nstrips * a.nsegs) return;
 
-    T* ring = reinterpret_cast<T*>(smem_raw) + (size_t)warp * kInvSlots * Lay::SLOT;
+    S* ring = reinterpret_cast<S*>(smem_raw) + (size_t)warp * kInvSlots * Lay::SLOT;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kInvWarps * kInvSlots *
-                                                              Lay::SLOT * sizeof(T)) +
+                                                              Lay::SLOT * sizeof(S)) +
                      warp * kInvSlots;
 
     const int strip = wid % a.nstrips;
@@ -180,11 +178,11 @@ __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
     w.lane = lane;
     w.xb = strip * a.valid_px - a.xoff;
     w.lane_ok = lane >= a.lane_lo && lane < a.lane_hi;
-    w.out = reinterpret_cast<T*>(a.out);
+    w.out = reinterpret_cast<S*>(a.out);
     w.opitch = a.out_pitch;
     w.out_h = a.lv[0].h;
     w.out_w = a.lv[0].w;
-    w.vec_out = (a.out_pitch % 4) == 0;
+    w.vec_out = (a.out_pitch % (2 * Q1)) == 0;
     const int ne1 = (a.lv[0].h + 1) >> 1;
     w.A0 = seg * a.segq;
     w.A1 = min(w.A0 + a.segq, ne1);
@@ -194,7 +192,8 @@ __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
     const int ne_c1 = (a.lv[0].w + 1) >> 1, ne_r1 = ne1;
     w.x1 = make_ctx(g1w + Q1 * lane, Q1, a.lv[0].h, a.lv[0].w, a.lane_lo, a.lane_hi, a.lv[0].s);
     const int xh1 = ne_c1 + g1w, xl1 = g1w;
-    const int bx1h = xh1 & ~3, bx1l = xl1 & ~3;
+    constexpr int AM = Lay::A - 1;
+    const int bx1h = xh1 & ~AM, bx1l = xl1 & ~AM;
     w.o1h = xh1 - bx1h;
     w.o1l = xl1 - bx1l;
     bool hfast = g1w >= 2 && g1w + 32 * Q1 + 2 <= (a.lv[0].w >> 1);
@@ -205,8 +204,8 @@ __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
         ne_r2 = (a.lv[1].h + 1) >> 1;
         w.x2 = make_ctx(g2w + W::Q2 * lane, W::Q2, a.lv[1].h, a.lv[1].w, a.lane_lo, a.lane_hi, a.lv[1].s);
         const int xh2 = ne_c2 + g2w, xl2 = g2w;
-        bx2h = xh2 & ~3;
-        bx2l = xl2 & ~3;
+        bx2h = xh2 & ~AM;
+        bx2l = xl2 & ~AM;
         w.o2h = xh2 - bx2h;
         w.o2l = xl2 - bx2l;
         hfast = hfast && g2w >= 2 && g2w + 32 * W::Q2 + 2 <= (a.lv[1].w >> 1);
@@ -224,7 +223,7 @@ __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
     const uint32_t bar_s = smem_u32(bars);
     auto issue = [&](int s) {
         const int b = s % kInvSlots;
-        const uint32_t dst = ring_s + (uint32_t)(b * Lay::SLOT * sizeof(T));
+        const uint32_t dst = ring_s + (uint32_t)(b * Lay::SLOT * sizeof(S));
         const uint32_t bar = bar_s + 8 * b;
         const int q0 = qbase + 4 * s;
         const bool l1 = s >= PRO_SLOTS;
@@ -233,22 +232,22 @@ __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
         if (NL == 2) bytes += 4 * Lay::BYTES2;
         mbar_arrive_expect_tx(bar, bytes);
         if constexpr (NL == 1) {
-            tma_load_2d(dst + 0 * Lay::R1 * sizeof(T), &ml, bx1l, q0, bar);
-            tma_load_2d(dst + 1 * Lay::R1 * sizeof(T), &m1, bx1h, q0, bar);
-            tma_load_2d(dst + 2 * Lay::R1 * sizeof(T), &m1, bx1l, ne_r1 + q0, bar);
-            tma_load_2d(dst + 3 * Lay::R1 * sizeof(T), &m1, bx1h, ne_r1 + q0, bar);
+            tma_load_2d(dst + 0 * Lay::R1 * sizeof(S), &ml, bx1l, q0, bar);
+            tma_load_2d(dst + 1 * Lay::R1 * sizeof(S), &m1, bx1h, q0, bar);
+            tma_load_2d(dst + 2 * Lay::R1 * sizeof(S), &m1, bx1l, ne_r1 + q0, bar);
+            tma_load_2d(dst + 3 * Lay::R1 * sizeof(S), &m1, bx1h, ne_r1 + q0, bar);
         } else {
             if (l1) {
-                tma_load_2d(dst + 0 * Lay::R1 * sizeof(T), &m1, bx1h, q0, bar);
-                tma_load_2d(dst + 1 * Lay::R1 * sizeof(T), &m1, bx1l, ne_r1 + q0, bar);
-                tma_load_2d(dst + 2 * Lay::R1 * sizeof(T), &m1, bx1h, ne_r1 + q0, bar);
+                tma_load_2d(dst + 0 * Lay::R1 * sizeof(S), &m1, bx1h, q0, bar);
+                tma_load_2d(dst + 1 * Lay::R1 * sizeof(S), &m1, bx1l, ne_r1 + q0, bar);
+                tma_load_2d(dst + 2 * Lay::R1 * sizeof(S), &m1, bx1h, ne_r1 + q0, bar);
             }
-            const uint32_t d2 = dst + 3 * Lay::R1 * sizeof(T);
+            const uint32_t d2 = dst + 3 * Lay::R1 * sizeof(S);
             const int y2 = q0 / 2 + LAG;
-            tma_load_2d(d2 + 0 * Lay::R2 * sizeof(T), &ml, bx2l, y2, bar);
-            tma_load_2d(d2 + 1 * Lay::R2 * sizeof(T), &m2, bx2h, y2, bar);
-            tma_load_2d(d2 + 2 * Lay::R2 * sizeof(T), &m2, bx2l, ne_r2 + y2, bar);
-            tma_load_2d(d2 + 3 * Lay::R2 * sizeof(T), &m2, bx2h, ne_r2 + y2, bar);
+            tma_load_2d(d2 + 0 * Lay::R2 * sizeof(S), &ml, bx2l, y2, bar);
+            tma_load_2d(d2 + 1 * Lay::R2 * sizeof(S), &m2, bx2h, y2, bar);
+            tma_load_2d(d2 + 2 * Lay::R2 * sizeof(S), &m2, bx2l, ne_r2 + y2, bar);
+            tma_load_2d(d2 + 3 * Lay::R2 * sizeof(S), &m2, bx2h, ne_r2 + y2, bar);
         }
     };
     if (lane == 0) {
@@ -287,24 +286,19 @@ __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
 }
 
 size_t inv_tma_smem_bytes(int elem_bytes, int nl, int q1) {
-    const int W1 = 32 * q1 + 4, W2 = 32 * (q1 / 2) + 4;
-    const int R1 = round32(4 * W1), R2 = round32(2 * W2);
+    const int A = 16 / elem_bytes, E = 128 / elem_bytes;
+    const int W1 = 32 * q1 + A, W2 = 32 * (q1 / 2) + A;
+    const int R1 = (4 * W1 + E - 1) / E * E, R2 = (2 * W2 + E - 1) / E * E;
     const int slot = nl == 1 ? 4 * R1 : 3 * R1 + 4 * R2;
     return (size_t)kInvWarps * kInvSlots * slot * elem_bytes + (size_t)kInvWarps * kInvSlots * 8;
 }
 
-void inv_tma_boxes(int nl, int q1, int* box1, int* box2) {
-    *box1 = 32 * q1 + 4;
-    *box2 = 32 * (q1 / 2) + 4;
-    (void)nl;
-}
-
-template <class T, int SCH, int NL, int Q1>
+template <class S, int SCH, int NL, int Q1>
 static cudaError_t inv_launch_one(const CUtensorMap& m1, const CUtensorMap& m2,
                                   const CUtensorMap& ml, const FusedArgs& a, int grid,
                                   cudaStream_t st) {
-    auto k = inv_tma_kernel<T, SCH, NL, Q1>;
-    const size_t smem = inv_tma_smem_bytes(sizeof(T), NL, Q1);
+    auto k = inv_tma_kernel<S, SCH, NL, Q1>;
+    const size_t smem = inv_tma_smem_bytes(sizeof(S), NL, Q1);
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     k<<<grid, kInvWarps * 32, smem, st>>>(m1, m2, ml, a);
@@ -315,6 +309,11 @@ template <class T, int SCH>
 static cudaError_t inv_launch_nl(int nl, int q1, const CUtensorMap& m1, const CUtensorMap& m2,
                                  const CUtensorMap& ml, const FusedArgs& a, int grid,
                                  cudaStream_t st) {
+    if constexpr (sizeof(T) == 2) {  // 16-bit storage: 2 columns per lane
+        if (nl == 1) return inv_launch_one<T, SCH, 1, 2>(m1, m2, ml, a, grid, st);
+        if (nl == 2) return inv_launch_one<T, SCH, 2, 2>(m1, m2, ml, a, grid, st);
+        return cudaErrorInvalidValue;
+    }
     if (q1 == 2) {
         if (nl == 1) return inv_launch_one<T, SCH, 1, 2>(m1, m2, ml, a, grid, st);
         if (nl == 2) return inv_launch_one<T, SCH, 2, 2>(m1, m2, ml, a, grid, st);
@@ -340,8 +339,13 @@ static cudaError_t inv_launch_sch(int sch, int nl, int q1, const CUtensorMap& m1
 cudaError_t launch_inv_tma(int elem, int scheme, int nl, int q1, const CUtensorMap& m1,
                            const CUtensorMap& m2, const CUtensorMap& ml, const FusedArgs& a,
                            int grid, cudaStream_t st) {
-    if (elem == 0) return inv_launch_sch<float>(scheme, nl, q1, m1, m2, ml, a, grid, st);
-    return inv_launch_sch<int>(scheme, nl, q1, m1, m2, ml, a, grid, st);
+    switch (elem) {
+        case 0: return inv_launch_sch<float>(scheme, nl, q1, m1, m2, ml, a, grid, st);
+        case 1: return inv_launch_sch<int>(scheme, nl, q1, m1, m2, ml, a, grid, st);
+        case 2: return inv_launch_sch<__half>(scheme, nl, 2, m1, m2, ml, a, grid, st);
+        case 3: return inv_launch_sch<__nv_bfloat16>(scheme, nl, 2, m1, m2, ml, a, grid, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace dwt
