@@ -72,7 +72,9 @@ typedef enum {
     DWT2D_NONSEP_REDUCED = 2,       /* S_U | T_P with P = P0 + P1, U = U0 + U1 (Sec. 3) */
     DWT2D_SEPARABLE_MULTIPASS = 3,  /* one HBM round trip per step (shader mapping)    */
     DWT2D_NONSEP_MULTIPASS = 4,
-    DWT2D_NONSEP_REDUCED_MULTIPASS = 5
+    DWT2D_NONSEP_REDUCED_MULTIPASS = 5,
+    DWT2D_SEPARABLE_CONVOLUTION = 6 /* N^V | N^H: 9/7 filter bank per level (Sec. 2, Eq. 1);
+                                       CDF 9/7 only; its inverse runs the reduced lifting */
 } dwt2d_scheme;
 
 typedef enum { DWT2D_F32 = 0, DWT2D_I32 = 1, DWT2D_F16 = 2, DWT2D_BF16 = 3 } dwt2d_dtype;

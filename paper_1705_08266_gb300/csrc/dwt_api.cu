@@ -52,10 +52,37 @@ long long round_pitch(long long w, int elem) {
     return bytes / elem;
 }
 
-bool multipass(dwt2d_scheme s) { return s >= DWT2D_SEPARABLE_MULTIPASS; }
+bool multipass(dwt2d_scheme s) {
+    return s >= DWT2D_SEPARABLE_MULTIPASS && s <= DWT2D_NONSEP_REDUCED_MULTIPASS;
+}
+bool convolution(dwt2d_scheme s) { return s == DWT2D_SEPARABLE_CONVOLUTION; }
+
+// CDF 9/7 analysis filters (low: 9 taps, high: 7 taps, centred) derived from
+// the lifting steps: the impulse responses of one 1-D forward lifting pass
+// (Eq. 2 factors Eq. 1), computed in double precision.
+void cdf97_taps(float h0[9], float g0[7]) {
+    const double a = -1.586134342059924, b = -0.052980118572961, c = 0.882911075530934,
+                 d = 0.443506852043971, K = 1.230174104914001;
+    const int N = 40;
+    for (int p = 20; p <= 21; ++p) {
+        double x[N] = {0};
+        x[p] = 1.0;
+        const double pu[2][2] = {{a, b}, {c, d}};
+        for (int k = 0; k < 2; ++k) {
+            for (int i = 1; i + 1 < N; i += 2) x[i] += pu[k][0] * (x[i - 1] + x[i + 1]);
+            for (int i = 2; i + 1 < N; i += 2) x[i] += pu[k][1] * (x[i - 1] + x[i + 1]);
+        }
+        for (int n = 0; 2 * n < N; ++n) {
+            const int kh = p - 2 * n, kg = p - 2 * n - 1;
+            if (kh >= -4 && kh <= 4) h0[kh + 4] = (float)(x[2 * n] / K);
+            if (kg >= -3 && kg <= 3 && 2 * n + 1 < N) g0[kg + 3] = (float)(x[2 * n + 1] * K);
+        }
+    }
+}
 
 int base_scheme(dwt2d_scheme s) {
     switch (s) {
+        case DWT2D_SEPARABLE_CONVOLUTION: return SCH_RED;  // its inverse
         case DWT2D_SEPARABLE:
         case DWT2D_SEPARABLE_MULTIPASS: return SCH_SEP;
         case DWT2D_NONSEP:
@@ -412,6 +439,37 @@ dwt2d_status run_multipass(const dwt2d_plan_s* p, bool fwd, const void* src, int
     return DWT2D_OK;
 }
 
+dwt2d_status run_conv_fwd(const dwt2d_plan_s* p, const void* src, int64_t sp, void* dst, int64_t dp,
+                          void* ws, cudaStream_t st) {
+    const int elem_kind = elem_kind_of(p->dtype);
+    char* wsb = reinterpret_cast<char*>(ws);
+    void* LLb[2] = {wsb + p->off_a, wsb + p->off_b};
+    const long long llp[2] = {p->pitch_a, p->pitch_b};
+    const long long src_pe = sp / p->elem, dst_pe = dp / p->elem;
+    ConvArgs a;
+    memset(&a, 0, sizeof(a));
+    cdf97_taps(a.h0, a.g0);
+    const void* in = src;
+    long long in_p = src_pe;
+    for (int l = 0; l < p->levels; ++l) {
+        a.h = p->hs[l];
+        a.w = p->ws[l];
+        a.src = in;
+        a.src_pitch = in_p;
+        a.dst = dst;
+        a.dst_pitch = dst_pe;
+        const bool last = l == p->levels - 1;
+        a.ll = last ? dst : LLb[l & 1];
+        a.ll_pitch = last ? dst_pe : llp[l & 1];
+        mark(p, l, 0, st);
+        if (launch_conv_fwd(elem_kind, a, st) != cudaSuccess) return DWT2D_ERR_CUDA;
+        mark(p, l, 1, st);
+        in = a.ll;
+        in_p = a.ll_pitch;
+    }
+    return DWT2D_OK;
+}
+
 }  // namespace
 
 size_t dwt::plan_workspace_bytes(dwt2d_plan_t p) { return p ? p->ws_bytes : 0; }
@@ -426,7 +484,8 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
     if (height < 1 || width < 1 || height > 65536 || width > 65536) return DWT2D_ERR_INVALID;
     if (levels < 1 || levels > 16) return DWT2D_ERR_INVALID;
     if (boundary != DWT2D_SYMMETRIC_WHOLE) return DWT2D_ERR_UNSUPPORTED;
-    if (scheme < DWT2D_SEPARABLE || scheme > DWT2D_NONSEP_REDUCED_MULTIPASS) return DWT2D_ERR_INVALID;
+    if (scheme < DWT2D_SEPARABLE || scheme > DWT2D_SEPARABLE_CONVOLUTION) return DWT2D_ERR_INVALID;
+    if (convolution(scheme) && wavelet != DWT2D_CDF97) return DWT2D_ERR_UNSUPPORTED;
     const bool half = dtype == DWT2D_F16 || dtype == DWT2D_BF16;
     if (!((wavelet == DWT2D_CDF97 && (dtype == DWT2D_F32 || half)) ||
           (wavelet == DWT2D_LEGALL53 && dtype == DWT2D_I32)))
@@ -487,7 +546,7 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
     };
     long long pa = 1, pb = 1;
     size_t ba = 0, bb = 0;
-    if (multipass(scheme)) {
+    if (multipass(scheme) || convolution(scheme)) {
         // LLs alternate between A and B in both directions; size both for LL of level 1
         if (levels > 1) {
             const int lh = (p->hs[0] + 1) / 2, lw = (p->ws[0] + 1) / 2;
@@ -550,6 +609,7 @@ dwt2d_status dwt2d_forward(dwt2d_plan_t p, const void* d_src, int64_t sp, void* 
     if (s == DWT2D_OK && !scale_ok(p, scale)) s = DWT2D_ERR_INVALID;
     if (s != DWT2D_OK) return s;
     if (d_src == d_dst) return DWT2D_ERR_INVALID;
+    if (convolution(p->scheme)) return run_conv_fwd(p, d_src, sp, d_dst, dp, d_ws, as_stream(stream));
     return multipass(p->scheme) ? run_multipass(p, true, d_src, sp, d_dst, dp, d_ws, as_stream(stream))
                                 : run_fused(p, true, d_src, sp, d_dst, dp, d_ws, as_stream(stream));
 }
@@ -616,6 +676,13 @@ dwt2d_status dwt2d_workspace_status(void* d_ws, void* stream) {
 
 dwt2d_status dwt2d_plan_info(dwt2d_plan_t p, int32_t* launches, int32_t* fused, int32_t* n_groups) {
     if (!p) return DWT2D_ERR_INVALID;
+    if (convolution(p->scheme)) {
+        if (launches) *launches = p->levels;
+        if (n_groups) *n_groups = p->levels;
+        if (fused)
+            for (int l = 0; l < p->levels; ++l) fused[l] = 1;
+        return DWT2D_OK;
+    }
     if (multipass(p->scheme)) {
         int kinds[8];
         float coefs[8];

@@ -78,6 +78,20 @@ cudaError_t launch_inv_tma(int elem, int scheme, int nl, int q1, const CUtensorM
 size_t inv_tma_smem_bytes(int elem_bytes, int nl, int q1);
 constexpr int kInvTmaWarps = 4;
 
+// One level of the separable convolution scheme (Sec. 2, Eq. 1).
+struct ConvArgs {
+    int h, w;
+    const void* src;   // the level's input (image or LL), element pitch
+    long long src_pitch;
+    void* dst;         // Mallat array (detail bands of this level)
+    long long dst_pitch;
+    void* ll;          // LL output of this level
+    long long ll_pitch;
+    float h0[9];       // analysis low pass, centred (k = -4 .. 4)
+    float g0[7];       // analysis high pass, centred (k = -3 .. 3)
+};
+cudaError_t launch_conv_fwd(int elem, const ConvArgs& a, cudaStream_t st);
+
 // elem: 0 = float32, 1 = int32.  kind: the step (see dwt_multipass.cu).
 cudaError_t launch_pass(int elem, int kind, bool fwd, const PassArgs& a, cudaStream_t st);
 

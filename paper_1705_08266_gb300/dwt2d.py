@@ -28,6 +28,7 @@ SCHEMES = {
     "separable_multipass": 3,
     "nonsep_multipass": 4,
     "nonsep_reduced_multipass": 5,
+    "separable_convolution": 6,
 }
 DTYPES = {torch.float32: 0, torch.int32: 1, torch.float16: 2, torch.bfloat16: 3}
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "alignment", -4: "no memory",

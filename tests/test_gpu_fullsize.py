@@ -49,6 +49,8 @@ def _positions(rng):
 @pytest.mark.parametrize("wavelet", ["cdf97", "legall53"])
 @pytest.mark.parametrize("scheme", list(D.SCHEMES))
 def test_fullsize_sampled_and_round_trip(images, wavelet, scheme):
+    if wavelet == "legall53" and scheme == "separable_convolution":
+        pytest.skip("the convolution scheme is the linear CDF 9/7 filter bank")
     x = images[wavelet]
     plan = D.Plan(H, W, LEVELS, wavelet, scheme)
     ws = plan.workspace()

@@ -47,7 +47,7 @@ def _gpu():
 
 
 @pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
-@pytest.mark.parametrize("scheme", ["nonsep_reduced", "separable", "nonsep"])
+@pytest.mark.parametrize("scheme", ["nonsep_reduced", "separable", "nonsep", "separable_convolution"])
 @pytest.mark.parametrize("shape,levels", [((1030, 2050), 6), ((777, 513), 4), ((64, 300), 3)])
 def test_16bit_forward_and_inverse(dtype, scheme, shape, levels):
     h, w = shape
