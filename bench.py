@@ -342,6 +342,7 @@ def main():
     if not args.no_variants:
         out["variants"] = variants(D, synth, dev, stream, x, dst)
         out["precision_16384x16384_l6"] = precision_variants(D, synth, dev, stream)
+        out["batch_256_mixed"] = batch_variants(D, synth, dev, stream)
 
     if args.no_e2e:
         if rank == 0:
@@ -442,6 +443,76 @@ def precision_variants(D, synth, dev, stream):
                                           "strict_frac": round(strict / (ms / 1e3) / 1e9 / hbm, 4)}
         del x, c, y, wsb
         torch.cuda.empty_cache()
+    return res
+
+
+def batch_variants(D, synth, dev, stream):
+    """Batched forward transforms: 256 images, H and W uniform on 65..4096,
+    levels uniform on 1..6, 75% CDF 9/7 float32 and 25% LeGall 5/3 int32
+    (seed 2017).  One batch (eager, replayed from a CUDA graph, and with the
+    autotuned launch shape) against one dwt2d_forward call per image (eager and
+    captured in one CUDA graph)."""
+    from paper_1705_08266_gb300 import autotune
+
+    rng = np.random.default_rng(2017)
+    iters, warm = 10, 3
+    base = {"cdf97": torch.from_numpy(synth.gradient_noise(4096, 4096, 2017)).to(dev),
+            "legall53": torch.from_numpy(synth.uniform_int(4096, 4096, 2017)).to(dev)}
+    jobs, plans, wss = [], [], []
+    px = 0
+    for i in range(256):
+        h, w = int(rng.integers(65, 4097)), int(rng.integers(65, 4097))
+        lv = int(rng.integers(1, 7))
+        wav = "cdf97" if rng.random() < 0.75 else "legall53"
+        dt = torch.float32 if wav == "cdf97" else torch.int32
+        x = D.empty_image(h, w, dt, dev)
+        x.copy_(base[wav][:h, :w])
+        jobs.append((x, D.empty_image(h, w, dt, dev), lv, wav, 0))
+        plans.append(D.Plan(h, w, lv, wav))
+        wss.append(plans[-1].workspace(dev))
+        px += h * w
+    batch = D.Batch(jobs)
+    bws = batch.workspace(dev)
+    batch.upload(bws, stream=stream)
+    res = {"workload": "256 images, H,W ~ U{65..4096}, levels ~ U{1..6}, 75% CDF 9/7 f32 / "
+                       "25% LeGall 5/3 i32, forward, non-separable reduced lifting, seed 2017",
+           "images": 256, "pixels": px, "batch_launches": batch.info()[0],
+           "per_image_launches": sum(p.info()[0] for p in plans)}
+
+    def per_image():
+        for p, (s_, d_, _lv, _w, _i), w_ in zip(plans, jobs, wss):
+            p.forward(s_, d_, w_, stream=stream)
+
+    def batched():
+        batch.launch(bws, stream=stream)
+
+    for name, fn in (("per_image_eager", per_image), ("batch_eager", batched)):
+        for _ in range(warm):
+            fn()
+        ms = time_calls(fn, iters, stream)
+        res[name] = {"ms": round(ms, 4), "gpx_s": round(px / ms / 1e6, 1)}
+    for name, fn in (("per_image_graph", per_image), ("batch_graph", batched)):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+        with torch.cuda.stream(stream):  # replay on the timed stream
+            for _ in range(warm):
+                g.replay()
+            ms = time_calls(g.replay, iters, stream)
+        res[name] = {"ms": round(ms, 4), "gpx_s": round(px / ms / 1e6, 1)}
+        del g
+    with tempfile.TemporaryDirectory() as tmp:
+        best = autotune.tune(jobs, cache_path=os.path.join(tmp, "tune.json"), stream=stream)
+    tb = D.Batch(jobs, tuning=best)
+    tws = tb.workspace(dev)
+    tb.upload(tws, stream=stream)
+    fn = lambda: tb.launch(tws, stream=stream)  # noqa: E731
+    for _ in range(warm):
+        fn()
+    ms = time_calls(fn, iters, stream)
+    res["batch_autotuned"] = {"ms": round(ms, 4), "gpx_s": round(px / ms / 1e6, 1), "tuning": best,
+                              "launches": tb.info()[0]}
+    torch.cuda.synchronize()
     return res
 
 

@@ -219,6 +219,64 @@ dwt2d_status dwt2d_plan_set_launch_events(dwt2d_plan_t plan, void** events, int3
 dwt2d_status dwt2d_forward_noalloc(dwt2d_plan_t plan, const void* d_src, int64_t src_pitch_bytes,
                                    void* d_dst, int64_t dst_pitch_bytes, float scale, void* stream);
 
+/*
+ * Batched transforms -- many images of different sizes, level counts,
+ * wavelets, storage types and directions in a few launches.  (The paper
+ * transforms one image at a time; this is a library service for workloads of
+ * many small images, where per-image launches are latency-bound.)
+ *
+ * Images are processed in phases: phase k runs level group k of every forward
+ * image (fine to coarse) and level group (groups - 1 - k) of every inverse
+ * image (coarse to fine).  Within a phase, one launch covers every image of
+ * the same direction, storage type and fusion depth: its warps walk a table of
+ * per-image descriptors (geometry and TMA tensor maps) in device memory.
+ */
+typedef struct dwt2d_batch_s* dwt2d_batch_t;
+
+typedef struct {
+    int32_t height, width, levels;
+    dwt2d_wavelet wavelet;
+    dwt2d_dtype dtype;
+    int32_t inverse;          /* 0: image -> coefficients, 1: coefficients -> image */
+    const void* d_src;        /* device, 16-byte aligned, pitch a multiple of 16 */
+    int64_t src_pitch_bytes;
+    void* d_dst;              /* device, must not overlap d_src */
+    int64_t dst_pitch_bytes;
+} dwt2d_batch_item;
+
+/* Tuning knobs (0 = library default): levels fused in the first launch of an
+ * image (1 or 2; default 2), at most per later launch (1 or 2; default 2),
+ * warps per SM that the rows of one launch are cut into (default 48; the
+ * batched kernels keep 12 warps per SM resident, so 48 is four waves), and the
+ * smallest row segment of a warp (quadruple rows of the last fused level;
+ * default 2).  Every warp of a launch streams the same number of rows. */
+typedef struct {
+    int32_t fuse_first, fuse_max, warps_per_sm, min_segment;
+} dwt2d_tuning;
+
+/*
+ * dwt2d_batch_create -- validate n items (each as dwt2d_plan would, plus its
+ *   buffers as dwt2d_forward would) for one lifting scheme (DWT2D_SEPARABLE,
+ *   DWT2D_NONSEP or DWT2D_NONSEP_REDUCED) and plan the launches.  The items
+ *   are copied; their buffers must stay valid while the batch is used.
+ *   tuning may be NULL.  workspace_bytes receives the device workspace the
+ *   batch needs (descriptor tables + inter-launch LL buffers + status word).
+ * dwt2d_batch_upload -- write the descriptor tables into d_workspace
+ *   (asynchronous on stream; not capturable: call it before any capture).
+ *   Zeroes the status word.
+ * dwt2d_batch_launch -- launch every kernel of the batch on stream; kernel
+ *   launches only, so it can be captured in a CUDA graph and replayed.  The
+ *   workspace must have been uploaded for this batch.
+ * dwt2d_batch_info -- kernel launches per dwt2d_batch_launch and warps in all.
+ */
+dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* items, int32_t n,
+                                dwt2d_scheme scheme, const dwt2d_tuning* tuning,
+                                size_t* workspace_bytes);
+dwt2d_status dwt2d_batch_upload(dwt2d_batch_t batch, void* d_workspace, void* stream);
+dwt2d_status dwt2d_batch_launch(dwt2d_batch_t batch, void* d_workspace, void* stream);
+dwt2d_status dwt2d_batch_info(dwt2d_batch_t batch, int32_t* launches, int64_t* warps);
+void dwt2d_batch_destroy(dwt2d_batch_t batch);
+
 void dwt2d_plan_destroy(dwt2d_plan_t plan);
 const char* dwt2d_status_string(dwt2d_status status);
 

@@ -1,7 +1,8 @@
 """Build libdwt2d.so (sm_103a) in-tree with nvcc.
 
-Every .cu file under csrc/ is compiled in parallel, then linked into one
-shared library next to this file.  Usage: python -m paper_1705_08266_gb300.build
+Every .cu file under csrc/ is compiled in parallel by nvcc (host-only .cpp
+files by the host compiler), then linked into one shared library next to this
+file.  Usage: python -m paper_1705_08266_gb300.build
 """
 from __future__ import annotations
 
@@ -31,15 +32,25 @@ def nvcc() -> str:
 
 
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
+
+
+def cuda_include() -> str:
+    return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "include")
 
 
 def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+    stem, ext = os.path.splitext(os.path.basename(src))
+    obj = os.path.join(BUILD, stem + ".o")
+    if ext == ".cpp":
+        cxx = os.environ.get("CXX") or shutil.which("g++") or "g++"
+        cmd = [cxx, "-O2", "-std=c++20", "-fPIC", "-Wall", "-I", cuda_include(), "-I", INCLUDE,
+               "-I", CSRC, "-c", src, "-o", obj]
+    else:
+        cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        raise RuntimeError(f"compile failed for {src}:\n{r.stdout}\n{r.stderr}")
     return obj
 
 

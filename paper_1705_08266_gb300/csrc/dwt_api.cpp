@@ -4,7 +4,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "dwt2d.h"
 #include "dwt_internal.h"
@@ -43,6 +45,28 @@ struct dwt2d_plan_s {
     // profiling hook: events[2i] / events[2i+1] around launch i
     cudaEvent_t* events;
     int nevents;
+};
+
+// A batch: per-image plans, workspace regions and the launch list.
+struct dwt2d_batch_s {
+    struct Launch {
+        int fwd, elem_kind, nl;
+        int first, count;  // entries [first, first + count) of the table
+        int grid;
+    };
+    dwt2d_scheme scheme;
+    std::vector<dwt2d_batch_item> items;
+    std::vector<dwt2d_plan_s*> plans;
+    std::vector<size_t> region;             // workspace offset of each image's LL buffers
+    std::vector<Launch> launches;            // in issue order
+    std::vector<std::pair<int, int>> refs;   // table entry -> (image, launch k of the image)
+    std::vector<int> segq;                   // table entry -> rows per warp (quadruple rows)
+    std::vector<dwt::BatchEntry> table;      // host copy, filled at upload
+    size_t table_off, ws_bytes;
+    long long warps;
+    ~dwt2d_batch_s() {
+        for (auto* p : plans) free(p);
+    }
 };
 
 namespace {
@@ -178,8 +202,9 @@ dwt2d_status check_buffers(const dwt2d_plan_s* p, const void* src, int64_t sp, c
 }
 
 // Warp work decomposition of one streaming launch.
+// Rows per warp: enough segments for target_warps warps, or segq_fixed (> 0).
 void decompose(const dwt2d_plan_s* p, int w_first, int rows, int nl, int rho, int q1,
-               int target_warps, FusedArgs* a, int* grid, int warps_per_block) {
+               int target_warps, FusedArgs* a, int* grid, int warps_per_block, int segq_fixed = 0) {
     valid_lanes(nl, rho, q1, &a->lane_lo, &a->lane_hi);
     const int qn = q1 >> (nl - 1);
     const int ppl = qn * (1 << nl);  // input pixels per lane
@@ -190,9 +215,12 @@ void decompose(const dwt2d_plan_s* p, int w_first, int rows, int nl, int rho, in
     a->valid_px = (a->lane_hi - a->lane_lo) * ppl;
     a->xoff = a->lane_lo * ppl;
     a->nstrips = (w_first + a->valid_px - 1) / a->valid_px;
-    int nsegs = target_warps / a->nstrips;
-    if (nsegs < 1) nsegs = 1;
-    int segq = (rows + nsegs - 1) / nsegs;
+    int segq = segq_fixed;
+    if (segq <= 0) {
+        int nsegs = target_warps / a->nstrips;
+        if (nsegs < 1) nsegs = 1;
+        segq = (rows + nsegs - 1) / nsegs;
+    }
     if (segq < p->min_segq) segq = p->min_segq;
     if (segq > rows) segq = rows;
     if (segq < 1) segq = 1;
@@ -217,103 +245,122 @@ int elem_kind_of(dwt2d_dtype d) {
     }
 }
 
-dwt2d_status run_fused(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t sp, void* dst,
-                       int64_t dp, void* ws, cudaStream_t st) {
+// One streaming launch of a plan: level group `gi`, its argument block, its
+// tensor maps and its grid.
+struct GroupLaunch {
+    int path;  // 0: forward (TMA); 1: inverse (TMA ring); 2: inverse (row-wise loads)
+    int nl, q1, grid;
+    FusedArgs a;
+    CUtensorMap m[3];
+};
+
+// Launch k of a plan in its direction (forward: group k; inverse: group
+// ngroups - 1 - k).  Inter-launch LL buffers live in the plan's workspace
+// layout at `ws`; the status word is `err`.
+dwt2d_status build_group(const dwt2d_plan_s* p, bool fwd, int k, const void* src, long long src_pe,
+                         void* dst, long long dst_pe, char* ws, int* err, int fwd_target,
+                         int inv_target, GroupLaunch* out, int segq_fixed = 0) {
     const int elem_kind = elem_kind_of(p->dtype);
     const int rho = p->wavelet == DWT2D_CDF97 ? 2 : 1;
-    const int sch = base_scheme(p->scheme);
-    char* wsb = reinterpret_cast<char*>(ws);
-    int* err = reinterpret_cast<int*>(wsb);
-    void* bufs[2] = {wsb + p->off_a, wsb + p->off_b};
+    void* bufs[2] = {ws + p->off_a, ws + p->off_b};
     const long long bpitch[2] = {p->pitch_a, p->pitch_b};
-    const long long src_pe = sp / p->elem, dst_pe = dp / p->elem;
-
+    FusedArgs& a = out->a;
+    memset(&a, 0, sizeof(a));
+    a.err = err;
     if (fwd) {
-        const void* in = src;
-        long long in_pitch = src_pe;
-        for (int gi = 0; gi < p->ngroups; ++gi) {
-            const Group g = p->groups[gi];
-            FusedArgs a;
-            memset(&a, 0, sizeof(a));
-            for (int i = 0; i < g.n; ++i) {
-                a.lv[i].h = p->hs[g.first + i];
-                a.lv[i].w = p->ws[g.first + i];
-                level_scale(a.lv[i].h, a.lv[i].w, false, a.lv[i].s);
-            }
-            a.mallat = dst;
-            a.mallat_pitch = dst_pe;
-            const bool last = gi == p->ngroups - 1;
-            a.ll = last ? dst : bufs[gi & 1];
-            a.ll_pitch = last ? dst_pe : bpitch[gi & 1];
-            a.err = err;
-            const int q1 = g.n >= 3 ? 4 : p->fwd_q1;
-            CUtensorMap map;
-            dwt2d_status s = make_map(&map, in, a.lv[0].h, a.lv[0].w, in_pitch, p->elem, elem_kind,
-                                      64 * q1);
-            if (s != DWT2D_OK) return s;
-            const int hN = a.lv[g.n - 1].h;
-            int grid;
-            decompose(p, a.lv[0].w, (hN + 1) / 2, g.n, rho, q1, p->fwd_warps_target, &a, &grid,
-                      kFwdWarps);
-            mark(p, gi, 0, st);
-            if (launch_fwd_fused(elem_kind, sch, g.n, q1, map, a, grid, st) != cudaSuccess)
-                return DWT2D_ERR_CUDA;
-            mark(p, gi, 1, st);
-            in = a.ll;
-            in_pitch = a.ll_pitch;
-        }
-        return DWT2D_OK;
-    }
-    // inverse: coarse group first
-    const void* ll_in = src;  // the coarsest LL sits at the top-left of the Mallat array
-    long long ll_pitch = src_pe;
-    for (int gi = p->ngroups - 1, k = 0; gi >= 0; --gi, ++k) {
+        const int gi = k;
         const Group g = p->groups[gi];
-        FusedArgs a;
-        memset(&a, 0, sizeof(a));
         for (int i = 0; i < g.n; ++i) {
             a.lv[i].h = p->hs[g.first + i];
             a.lv[i].w = p->ws[g.first + i];
-            level_scale(a.lv[i].h, a.lv[i].w, true, a.lv[i].s);
+            level_scale(a.lv[i].h, a.lv[i].w, false, a.lv[i].s);
         }
-        a.mallat = const_cast<void*>(src);
-        a.mallat_pitch = src_pe;
-        a.ll = const_cast<void*>(ll_in);
-        a.ll_pitch = ll_pitch;
-        const bool last = gi == 0;
-        a.out = last ? dst : bufs[k & 1];
-        a.out_pitch = last ? dst_pe : bpitch[k & 1];
-        a.err = err;
-        int grid;
-        if (g.n <= 2) {
-            // TMA ring: boxes of the Mallat array and of the LL source
-            const int q1 = p->inv_q1;
-            const int al = 16 / p->elem;  // boxes start at a 16-byte boundary
-            const int w1 = 32 * q1 + al, w2 = 16 * q1 + al;
-            const int kind = elem_kind;
-            CUtensorMap m1, m2, ml;
-            dwt2d_status s = make_map(&m1, src, p->H, p->W, src_pe, p->elem, kind, w1, 4);
-            if (s == DWT2D_OK) s = make_map(&m2, src, p->H, p->W, src_pe, p->elem, kind, w2, 2);
-            const int llh = (a.lv[g.n - 1].h + 1) / 2, llw = (a.lv[g.n - 1].w + 1) / 2;
-            const bool ll_is_src = ll_in == src;
-            if (s == DWT2D_OK)
-                s = make_map(&ml, ll_in, ll_is_src ? p->H : llh, ll_is_src ? p->W : llw, ll_pitch,
-                             p->elem, kind, g.n == 1 ? w1 : w2, g.n == 1 ? 4 : 2);
-            if (s != DWT2D_OK) return s;
-            decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, q1, p->inv_warps_target, &a, &grid,
-                      kInvTmaWarps);
-            mark(p, k, 0, st);
-            if (launch_inv_tma(elem_kind, sch, g.n, q1, m1, m2, ml, a, grid, st) != cudaSuccess)
-                return DWT2D_ERR_CUDA;
-            mark(p, k, 1, st);
-        } else {
-            decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, 4, p->inv_warps_target, &a, &grid, 4);
-            mark(p, k, 0, st);
-            if (launch_inv_fused(elem_kind, sch, g.n, a, grid, st) != cudaSuccess) return DWT2D_ERR_CUDA;
-            mark(p, k, 1, st);
-        }
-        ll_in = a.out;
-        ll_pitch = a.out_pitch;
+        // input: the image, else the LL the previous launch wrote
+        const void* in = gi == 0 ? src : bufs[(gi - 1) & 1];
+        const long long in_pitch = gi == 0 ? src_pe : bpitch[(gi - 1) & 1];
+        a.mallat = dst;
+        a.mallat_pitch = dst_pe;
+        const bool last = gi == p->ngroups - 1;
+        a.ll = last ? dst : bufs[gi & 1];
+        a.ll_pitch = last ? dst_pe : bpitch[gi & 1];
+        const int q1 = g.n >= 3 ? 4 : p->fwd_q1;
+        dwt2d_status s = make_map(&out->m[0], in, a.lv[0].h, a.lv[0].w, in_pitch, p->elem, elem_kind,
+                                  64 * q1);
+        if (s != DWT2D_OK) return s;
+        const int hN = a.lv[g.n - 1].h;
+        decompose(p, a.lv[0].w, (hN + 1) / 2, g.n, rho, q1, fwd_target, &a, &out->grid, kFwdWarps,
+                  segq_fixed);
+        out->path = 0;
+        out->nl = g.n;
+        out->q1 = q1;
+        return DWT2D_OK;
+    }
+    // inverse: coarse group first; the coarsest LL sits at the top-left of the
+    // Mallat array, later ones in the buffer the previous launch wrote
+    const int gi = p->ngroups - 1 - k;
+    const Group g = p->groups[gi];
+    for (int i = 0; i < g.n; ++i) {
+        a.lv[i].h = p->hs[g.first + i];
+        a.lv[i].w = p->ws[g.first + i];
+        level_scale(a.lv[i].h, a.lv[i].w, true, a.lv[i].s);
+    }
+    const void* ll_in = k == 0 ? src : bufs[(k - 1) & 1];
+    const long long ll_pitch = k == 0 ? src_pe : bpitch[(k - 1) & 1];
+    a.mallat = const_cast<void*>(src);
+    a.mallat_pitch = src_pe;
+    a.ll = const_cast<void*>(ll_in);
+    a.ll_pitch = ll_pitch;
+    const bool last = gi == 0;
+    a.out = last ? dst : bufs[k & 1];
+    a.out_pitch = last ? dst_pe : bpitch[k & 1];
+    out->nl = g.n;
+    if (g.n <= 2) {
+        // TMA ring: boxes of the Mallat array and of the LL source
+        const int q1 = p->inv_q1;
+        const int al = 16 / p->elem;  // boxes start at a 16-byte boundary
+        const int w1 = 32 * q1 + al, w2 = 16 * q1 + al;
+        dwt2d_status s = make_map(&out->m[0], src, p->H, p->W, src_pe, p->elem, elem_kind, w1, 4);
+        if (s == DWT2D_OK) s = make_map(&out->m[1], src, p->H, p->W, src_pe, p->elem, elem_kind, w2, 2);
+        const int llh = (a.lv[g.n - 1].h + 1) / 2, llw = (a.lv[g.n - 1].w + 1) / 2;
+        const bool ll_is_src = k == 0;
+        if (s == DWT2D_OK)
+            s = make_map(&out->m[2], ll_in, ll_is_src ? p->H : llh, ll_is_src ? p->W : llw, ll_pitch,
+                         p->elem, elem_kind, g.n == 1 ? w1 : w2, g.n == 1 ? 4 : 2);
+        if (s != DWT2D_OK) return s;
+        decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, q1, inv_target, &a, &out->grid,
+                  kInvTmaWarps, segq_fixed);
+        out->path = 1;
+        out->q1 = q1;
+    } else {
+        decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, 4, inv_target, &a, &out->grid, 4);
+        out->path = 2;
+        out->q1 = 4;
+    }
+    return DWT2D_OK;
+}
+
+dwt2d_status run_fused(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t sp, void* dst,
+                       int64_t dp, void* ws, cudaStream_t st) {
+    const int elem_kind = elem_kind_of(p->dtype);
+    const int sch = base_scheme(p->scheme);
+    char* wsb = reinterpret_cast<char*>(ws);
+    int* err = reinterpret_cast<int*>(wsb);
+    for (int k = 0; k < p->ngroups; ++k) {
+        GroupLaunch gl;
+        dwt2d_status s = build_group(p, fwd, k, src, sp / p->elem, dst, dp / p->elem, wsb, err,
+                                     p->fwd_warps_target, p->inv_warps_target, &gl);
+        if (s != DWT2D_OK) return s;
+        cudaError_t e;
+        mark(p, k, 0, st);
+        if (gl.path == 0)
+            e = launch_fwd_fused(elem_kind, sch, gl.nl, gl.q1, gl.m[0], gl.a, gl.grid, st);
+        else if (gl.path == 1)
+            e = launch_inv_tma(elem_kind, sch, gl.nl, gl.q1, gl.m[0], gl.m[1], gl.m[2], gl.a, gl.grid,
+                               st);
+        else
+            e = launch_inv_fused(elem_kind, sch, gl.nl, gl.a, gl.grid, st);
+        if (e != cudaSuccess) return DWT2D_ERR_CUDA;
+        mark(p, k, 1, st);
     }
     return DWT2D_OK;
 }
@@ -476,9 +523,22 @@ size_t dwt::plan_workspace_bytes(dwt2d_plan_t p) { return p ? p->ws_bytes : 0; }
 
 extern "C" {
 
+static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,
+                                dwt2d_wavelet wavelet, dwt2d_scheme scheme, dwt2d_boundary boundary,
+                                dwt2d_dtype dtype, size_t* workspace_bytes, const dwt2d_tuning* tuning);
+
 dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,
                         dwt2d_wavelet wavelet, dwt2d_scheme scheme, dwt2d_boundary boundary,
                         dwt2d_dtype dtype, size_t* workspace_bytes) {
+    return plan_create(out, height, width, levels, wavelet, scheme, boundary, dtype, workspace_bytes,
+                       nullptr);
+}
+
+}  // extern "C"
+
+static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,
+                                dwt2d_wavelet wavelet, dwt2d_scheme scheme, dwt2d_boundary boundary,
+                                dwt2d_dtype dtype, size_t* workspace_bytes, const dwt2d_tuning* tuning) {
     if (!out || !workspace_bytes) return DWT2D_ERR_INVALID;
     *out = nullptr;
     if (height < 1 || width < 1 || height > 65536 || width > 65536) return DWT2D_ERR_INVALID;
@@ -510,11 +570,12 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
     // level groups: the first launch fuses DWT2D_FUSE_FIRST levels (default 2),
     // later launches up to DWT2D_FUSE (default 2; 3 needs 4 columns per lane,
     // which measured slower) each
-    int maxf = env_int("DWT2D_FUSE", 2);
+    int maxf = tuning && tuning->fuse_max > 0 ? tuning->fuse_max : env_int("DWT2D_FUSE", 2);
     if (maxf < 1) maxf = 1;
     if (maxf > kMaxFused) maxf = kMaxFused;
     if (half && maxf > 2) maxf = 2;  // 16-bit storage runs 2 columns per lane: up to 2 levels
-    int first = env_int("DWT2D_FUSE_FIRST", maxf < 2 ? maxf : 2);
+    int first = tuning && tuning->fuse_first > 0 ? tuning->fuse_first
+                                                 : env_int("DWT2D_FUSE_FIRST", maxf < 2 ? maxf : 2);
     if (first < 1) first = 1;
     if (first > maxf) first = maxf;
     p->ngroups = 0;
@@ -531,9 +592,11 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
     p->sm_count = sms;
-    p->fwd_warps_target = sms * env_int("DWT2D_FWD_WARPS_PER_SM", 16);
-    p->inv_warps_target = sms * env_int("DWT2D_INV_WARPS_PER_SM", 12);
-    p->min_segq = env_int("DWT2D_MIN_SEGQ", 2);
+    p->fwd_warps_target = sms * (tuning && tuning->warps_per_sm > 0 ? tuning->warps_per_sm
+                                                                    : env_int("DWT2D_FWD_WARPS_PER_SM", 16));
+    p->inv_warps_target = sms * (tuning && tuning->warps_per_sm > 0 ? tuning->warps_per_sm
+                                                                    : env_int("DWT2D_INV_WARPS_PER_SM", 12));
+    p->min_segq = tuning && tuning->min_segment > 0 ? tuning->min_segment : env_int("DWT2D_MIN_SEGQ", 2);
     p->fwd_q1 = env_int("DWT2D_FWD_Q", 2) == 4 && !half ? 4 : 2;
     p->inv_q1 = env_int("DWT2D_INV_Q", 2) == 4 && !half ? 4 : 2;
 
@@ -593,6 +656,8 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
     *out = p;
     return DWT2D_OK;
 }
+
+extern "C" {
 
 // 16-bit storage: stored value = value / scale for image and coefficients
 // alike.  The transform is linear, so the coefficients of the stored image are
@@ -708,6 +773,189 @@ dwt2d_status dwt2d_plan_set_launch_events(dwt2d_plan_t p, void** events, int32_t
 }
 
 void dwt2d_plan_destroy(dwt2d_plan_t p) { free(p); }
+
+dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* items, int32_t n,
+                                dwt2d_scheme scheme, const dwt2d_tuning* tuning,
+                                size_t* workspace_bytes) {
+    if (!out || !workspace_bytes || (n > 0 && !items) || n < 0) return DWT2D_ERR_INVALID;
+    *out = nullptr;
+    if (scheme != DWT2D_SEPARABLE && scheme != DWT2D_NONSEP && scheme != DWT2D_NONSEP_REDUCED)
+        return DWT2D_ERR_UNSUPPORTED;
+    dwt2d_tuning tun = {0, 0, 0, 0};
+    if (tuning) tun = *tuning;
+    // the batched kernels run 2 quadruple columns per lane: up to 2 fused levels
+    if (tun.fuse_max > 2 || tun.fuse_first > 2) return DWT2D_ERR_UNSUPPORTED;
+    if (tun.fuse_max <= 0) tun.fuse_max = 2;
+    const int wps = tun.warps_per_sm;
+    tun.warps_per_sm = 0;  // the per-image share is set below
+    dwt2d_batch_s* b = new (std::nothrow) dwt2d_batch_s();
+    if (!b) return DWT2D_ERR_NOMEM;
+    b->scheme = scheme;
+    b->items.assign(items, items + n);
+    size_t off = kHeader;
+    b->table_off = off;
+    for (int i = 0; i < n; ++i) {
+        const dwt2d_batch_item& it = items[i];
+        dwt2d_plan_t p = nullptr;
+        size_t wsb = 0;
+        dwt2d_status s = plan_create(&p, it.height, it.width, it.levels, it.wavelet, scheme,
+                                     DWT2D_SYMMETRIC_WHOLE, it.dtype, &wsb, &tun);
+        if (s == DWT2D_OK && (it.inverse != 0 && it.inverse != 1)) s = DWT2D_ERR_INVALID;
+        if (s == DWT2D_OK) s = check_buffers(p, it.d_src, it.src_pitch_bytes, it.d_dst,
+                                             it.dst_pitch_bytes, it.d_src);
+        if (s == DWT2D_OK && it.d_src == it.d_dst) s = DWT2D_ERR_INVALID;
+        if (s != DWT2D_OK) {
+            free(p);
+            delete b;
+            return s;
+        }
+        p->fwd_q1 = p->inv_q1 = 2;
+        b->plans.push_back(p);
+    }
+    // Launch list: phase k, then direction, storage type, fusion depth.  One
+    // launch spreads its rows evenly: every warp streams the same number of
+    // rows (segq), chosen so that the launch has about warps_per_sm warps per
+    // SM (default 48: four waves of the 12 resident, which evens out images
+    // whose border strips run the slower edge path).
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    int max_groups = 0;
+    for (auto* p : b->plans) max_groups = std::max(max_groups, p->ngroups);
+    b->warps = 0;
+    for (int k = 0; k < max_groups; ++k) {
+        for (int fwd = 1; fwd >= 0; --fwd) {
+            for (int ek = 0; ek < 4; ++ek) {
+                for (int nl = 1; nl <= 2; ++nl) {
+                    dwt2d_batch_s::Launch L = {fwd, ek, nl, (int)b->refs.size(), 0, 0};
+                    struct Cand { int i, w0, rows, rho, nstrips; };
+                    std::vector<Cand> cand;
+                    long long work = 0;  // strips x rows over the launch
+                    int min_segq = 1;
+                    for (int i = 0; i < n; ++i) {
+                        const dwt2d_plan_s* p = b->plans[i];
+                        if ((items[i].inverse == 0) != (fwd == 1) || elem_kind_of(p->dtype) != ek ||
+                            k >= p->ngroups)
+                            continue;
+                        const int gi = fwd ? k : p->ngroups - 1 - k;
+                        const Group g = p->groups[gi];
+                        if (g.n != nl) continue;
+                        Cand c;
+                        c.i = i;
+                        c.rho = p->wavelet == DWT2D_CDF97 ? 2 : 1;
+                        c.w0 = p->ws[g.first];
+                        c.rows = fwd ? (p->hs[g.first + g.n - 1] + 1) / 2 : (p->hs[g.first] + 1) / 2;
+                        FusedArgs a;
+                        memset(&a, 0, sizeof(a));
+                        int grid = 0;
+                        decompose(p, c.w0, c.rows, nl, c.rho, 2, 1, &a, &grid, 4);
+                        c.nstrips = a.nstrips;
+                        work += (long long)c.nstrips * c.rows;
+                        min_segq = std::max(min_segq, p->min_segq);
+                        cand.push_back(c);
+                    }
+                    if (cand.empty()) continue;
+                    const long long target = (long long)sms * (wps > 0 ? wps : 48);
+                    const int segq = (int)std::max<long long>(min_segq, (work + target - 1) / target);
+                    long long warps = 0;
+                    for (const Cand& c : cand) {
+                        const dwt2d_plan_s* p = b->plans[c.i];
+                        FusedArgs a;
+                        memset(&a, 0, sizeof(a));
+                        int grid = 0;
+                        decompose(p, c.w0, c.rows, nl, c.rho, 2, 1, &a, &grid, 4, segq);
+                        b->refs.push_back({c.i, k});
+                        b->segq.push_back(segq);
+                        warps += (long long)a.nstrips * a.nsegs;
+                        ++L.count;
+                    }
+                    if (warps > (1LL << 30)) {
+                        delete b;
+                        return DWT2D_ERR_INVALID;
+                    }
+                    L.grid = (int)((warps + 3) / 4);
+                    b->warps += warps;
+                    b->launches.push_back(L);
+                }
+            }
+        }
+    }
+    off += (b->refs.size() * sizeof(BatchEntry) + 255) / 256 * 256;
+    for (int i = 0; i < n; ++i) {
+        b->region.push_back(off);
+        off += (b->plans[i]->ws_bytes + 255) / 256 * 256;
+    }
+    b->ws_bytes = off;
+    *workspace_bytes = off;
+    *out = b;
+    return DWT2D_OK;
+}
+
+dwt2d_status dwt2d_batch_upload(dwt2d_batch_t b, void* d_ws, void* stream) {
+    if (!b || !d_ws) return DWT2D_ERR_INVALID;
+    if (!aligned16(d_ws) || ((uintptr_t)d_ws & 255u)) return DWT2D_ERR_ALIGN;
+    cudaStream_t st = as_stream(stream);
+    char* wsb = reinterpret_cast<char*>(d_ws);
+    int* err = reinterpret_cast<int*>(wsb);
+    b->table.assign(b->refs.size(), BatchEntry{});
+    for (const auto& L : b->launches) {
+        int first_warp = 0;
+        for (int j = L.first; j < L.first + L.count; ++j) {
+            const int i = b->refs[j].first, k = b->refs[j].second;
+            const dwt2d_batch_item& it = b->items[i];
+            const dwt2d_plan_s* p = b->plans[i];
+            GroupLaunch gl;
+            dwt2d_status s = build_group(p, it.inverse == 0, k, it.d_src, it.src_pitch_bytes / p->elem,
+                                         it.d_dst, it.dst_pitch_bytes / p->elem, wsb + b->region[i],
+                                         err, 1, 1, &gl, b->segq[j]);
+            if (s != DWT2D_OK) return s;
+            if (gl.path == 2 || gl.nl != L.nl) return DWT2D_ERR_INVALID;  // planned otherwise
+            BatchEntry& e = b->table[j];
+            memcpy(e.m, gl.m, sizeof(e.m));
+            e.args = gl.a;
+            e.first_warp = first_warp;
+            first_warp += gl.a.nstrips * gl.a.nsegs;
+        }
+        // kernel attributes once, outside any capture
+        const int sch = base_scheme(b->scheme);
+        const cudaError_t e = L.fwd ? launch_fwd_batched(L.elem_kind, sch, L.nl, nullptr, 0, 0, st)
+                                    : launch_inv_batched(L.elem_kind, sch, L.nl, nullptr, 0, 0, st);
+        if (e != cudaSuccess) return DWT2D_ERR_CUDA;
+    }
+    if (!b->table.empty() &&
+        cudaMemcpyAsync(wsb + b->table_off, b->table.data(), b->table.size() * sizeof(BatchEntry),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return DWT2D_ERR_CUDA;
+    if (cudaMemsetAsync(d_ws, 0, sizeof(int), st) != cudaSuccess) return DWT2D_ERR_CUDA;
+    return DWT2D_OK;
+}
+
+dwt2d_status dwt2d_batch_launch(dwt2d_batch_t b, void* d_ws, void* stream) {
+    if (!b || !d_ws) return DWT2D_ERR_INVALID;
+    if ((uintptr_t)d_ws & 255u) return DWT2D_ERR_ALIGN;
+    if (b->table.size() != b->refs.size()) return DWT2D_ERR_INVALID;  // not uploaded
+    cudaStream_t st = as_stream(stream);
+    const BatchEntry* table =
+        reinterpret_cast<const BatchEntry*>(reinterpret_cast<char*>(d_ws) + b->table_off);
+    const int sch = base_scheme(b->scheme);
+    for (const auto& L : b->launches) {
+        const cudaError_t e =
+            L.fwd ? launch_fwd_batched(L.elem_kind, sch, L.nl, table + L.first, L.count, L.grid, st)
+                  : launch_inv_batched(L.elem_kind, sch, L.nl, table + L.first, L.count, L.grid, st);
+        if (e != cudaSuccess) return DWT2D_ERR_CUDA;
+    }
+    return DWT2D_OK;
+}
+
+dwt2d_status dwt2d_batch_info(dwt2d_batch_t b, int32_t* launches, int64_t* warps) {
+    if (!b) return DWT2D_ERR_INVALID;
+    if (launches) *launches = (int32_t)b->launches.size();
+    if (warps) *warps = b->warps;
+    return DWT2D_OK;
+}
+
+void dwt2d_batch_destroy(dwt2d_batch_t b) { delete b; }
 
 const char* dwt2d_status_string(dwt2d_status s) {
     switch (s) {

@@ -193,10 +193,11 @@ __device__ __forceinline__ bool rows_interior(int q0, int nl, int lag, const int
 template <int Q1>
 __host__ __device__ constexpr int fwd_min_blocks() { return Q1 <= 2 ? 4 : 2; }
 
+// One warp's work item `wid` of a launch described by `a` (input through the
+// tensor map at `mapp`).
 template <class S, int SCH, int NL, int Q1>
-__global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
-    fwd_fused_kernel(const __grid_constant__ CUtensorMap map, const FusedArgs a) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArgs& a, int wid,
+                                         unsigned char* smem_raw) {
     using FW = FwdWarp<S, SCH, NL, Q1>;
     using T = typename FW::T;
     constexpr int RHO = FW::LAG;
@@ -205,8 +206,6 @@ __global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int wid = blockIdx.x * kFwdWarps + warp;
-    if (wid >= a.nstrips * a.nsegs) return;
 
     constexpr int kSlotElems = kFwdSlotRows * BW;
     S* ring = reinterpret_cast<S*>(smem_raw) + (size_t)warp * kFwdSlots * kSlotElems;
@@ -282,7 +281,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
         fence_mbar_init();
         for (int s = 0; s < kFwdSlots && s < nslots; ++s) {
             mbar_arrive_expect_tx(bar_s + 8 * s, kSlotBytes);
-            tma_load_2d(ring_s + s * kSlotBytes, &map, xb, y0 + s * kFwdSlotRows, bar_s + 8 * s);
+            tma_load_2d(ring_s + s * kSlotBytes, mapp, xb, y0 + s * kFwdSlotRows, bar_s + 8 * s);
         }
     }
     __syncwarp();
@@ -305,7 +304,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
         if (lane == 0 && s + kFwdSlots < nslots) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar_s + 8 * b, kSlotBytes);
-            tma_load_2d(ring_s + b * kSlotBytes, &map, xb, y0 + (s + kFwdSlots) * kFwdSlotRows,
+            tma_load_2d(ring_s + b * kSlotBytes, mapp, xb, y0 + (s + kFwdSlots) * kFwdSlotRows,
                         bar_s + 8 * b);
         }
     }
@@ -315,6 +314,38 @@ __global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
         for (int t = s; t < nslots && t < s + kFwdSlots; ++t)
             mbar_wait_bounded(bar_s + 8 * (t % kFwdSlots), (t / kFwdSlots) & 1, kWaitBudget);
     }
+}
+
+template <class S, int SCH, int NL, int Q1>
+__global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
+    fwd_fused_kernel(const __grid_constant__ CUtensorMap map, const FusedArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int wid = blockIdx.x * kFwdWarps + (threadIdx.x >> 5);
+    if (wid >= a.nstrips * a.nsegs) return;
+    fwd_body<S, SCH, NL, Q1>(&map, a, wid, smem_raw);
+}
+
+// Many images in one launch: warp w of the grid works on entry i with
+// first[i] <= w < first[i + 1] of a table in device memory.  The arguments
+// come from registers instead of the constant bank, so the kernel gets the
+// register budget of 3 CTAs per SM (no spills) rather than 4.
+template <class S, int SCH, int NL, int Q1>
+__global__ void __launch_bounds__(kFwdWarps * 32, 3)
+    fwd_batched_kernel(const BatchEntry* __restrict__ table, int n) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int gw = blockIdx.x * kFwdWarps + (threadIdx.x >> 5);
+    int lo = 0, hi = n - 1;  // last entry with first <= gw
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (table[mid].first_warp <= gw) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchEntry& e = table[lo];
+    const int wid = gw - e.first_warp;
+    const FusedArgs a = e.args;  // registers: the body's stores cannot alias it
+    if (wid < 0 || wid >= a.nstrips * a.nsegs) return;
+    fence_tensormap_acquire(&e.m[0]);
+    fwd_body<S, SCH, NL, Q1>(&e.m[0], a, wid, smem_raw);
 }
 
 size_t fwd_smem_bytes(int elem_bytes, int q1) {
@@ -331,6 +362,42 @@ static cudaError_t launch_one(const CUtensorMap& map, const FusedArgs& a, int gr
     if (err != cudaSuccess) return err;
     k<<<grid, kFwdWarps * 32, smem, st>>>(map, a);
     return cudaGetLastError();
+}
+
+template <class S, int SCH, int NL>
+static cudaError_t launch_batched_one(const BatchEntry* table, int n, int grid, cudaStream_t st) {
+    auto k = fwd_batched_kernel<S, SCH, NL, 2>;
+    const size_t smem = fwd_smem_bytes(sizeof(S), 2);
+    if (grid == 0)
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, kFwdWarps * 32, smem, st>>>(table, n);
+    return cudaGetLastError();
+}
+
+template <class S>
+static cudaError_t launch_batched_s(int sch, int nl, const BatchEntry* table, int n, int grid,
+                                   cudaStream_t st) {
+    if (nl < 1 || nl > 2) return cudaErrorInvalidValue;
+    switch (sch) {
+        case SCH_SEP: return nl == 1 ? launch_batched_one<S, SCH_SEP, 1>(table, n, grid, st)
+                                     : launch_batched_one<S, SCH_SEP, 2>(table, n, grid, st);
+        case SCH_NONSEP: return nl == 1 ? launch_batched_one<S, SCH_NONSEP, 1>(table, n, grid, st)
+                                        : launch_batched_one<S, SCH_NONSEP, 2>(table, n, grid, st);
+        case SCH_RED: return nl == 1 ? launch_batched_one<S, SCH_RED, 1>(table, n, grid, st)
+                                     : launch_batched_one<S, SCH_RED, 2>(table, n, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fwd_batched(int elem, int scheme, int nl, const BatchEntry* table, int n, int grid,
+                               cudaStream_t st) {
+    switch (elem) {
+        case 0: return launch_batched_s<float>(scheme, nl, table, n, grid, st);
+        case 1: return launch_batched_s<int>(scheme, nl, table, n, grid, st);
+        case 2: return launch_batched_s<__half>(scheme, nl, table, n, grid, st);
+        case 3: return launch_batched_s<__nv_bfloat16>(scheme, nl, table, n, grid, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <class T, int SCH>

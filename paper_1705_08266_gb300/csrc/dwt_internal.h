@@ -56,12 +56,31 @@ struct PassArgs {
     int scale_in, scale_out;
 };
 
+// One image (one level group) of a batched launch, in device memory.  The
+// tensor maps (128-byte aligned) come first.  The forward uses m[0];
+// the inverse m[0] (Mallat, level-1 box), m[1] (Mallat, level-2 box), m[2]
+// (LL source).
+struct BatchEntry {
+    CUtensorMap m[3];
+    FusedArgs args;
+    int first_warp;  // first global warp of this entry in the launch
+};
+
 // Kernel-geometry constants of the streaming forward kernel.
 constexpr int kFwdWarps = 4;        // warps per CTA (each warp is independent)
 constexpr int kFwdSlots = 3;        // TMA ring depth per warp
 constexpr int kFwdSlotRows = 8;     // image rows per TMA box (4 quadruple rows)
 
 size_t fwd_smem_bytes(int elem_bytes, int q1);
+
+// Batched forward / inverse: entries of one element type, scheme and fusion
+// depth (1 or 2), 2 quadruple columns per lane; `grid` CTAs of 4 warps.
+// grid == 0 only sets the kernel's shared-memory attribute (done once, before
+// any stream capture), so a launch itself is a plain kernel launch.
+cudaError_t launch_fwd_batched(int elem, int scheme, int nl, const BatchEntry* table, int n, int grid,
+                               cudaStream_t st);
+cudaError_t launch_inv_batched(int elem, int scheme, int nl, const BatchEntry* table, int n, int grid,
+                               cudaStream_t st);
 
 // q1: quadruple columns per lane at the first fused level (2 or 4; 3 fused levels need 4)
 cudaError_t launch_fwd_fused(int elem, int scheme, int nl, int q1, const CUtensorMap& map,

@@ -151,10 +151,9 @@ __device__ __forceinline__ bool inv_rows_interior(int q0, int nl, int lag, const
 }
 
 template <class S, int SCH, int NL, int Q1>
-__global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
-    inv_tma_kernel(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2,
-                   const __grid_constant__ CUtensorMap ml, const FusedArgs a) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ void inv_body(const CUtensorMap* m1p, const CUtensorMap* m2p,
+                                         const CUtensorMap* mlp, const FusedArgs& a, int wid,
+                                         unsigned char* smem_raw) {
     using W = InvWarpT<S, SCH, NL, Q1>;
     using Lay = InvLayout<S, NL, Q1>;
     constexpr int LAG = W::LAG;
@@ -164,8 +163,6 @@ __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int wid = blockIdx.x * kInvWarps + warp;
-    if (wid >= a.nstrips * a.nsegs) return;
 
     S* ring = reinterpret_cast<S*>(smem_raw) + (size_t)warp * kInvSlots * Lay::SLOT;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kInvWarps * kInvSlots *
@@ -232,22 +229,22 @@ __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
         if (NL == 2) bytes += 4 * Lay::BYTES2;
         mbar_arrive_expect_tx(bar, bytes);
         if constexpr (NL == 1) {
-            tma_load_2d(dst + 0 * Lay::R1 * sizeof(S), &ml, bx1l, q0, bar);
-            tma_load_2d(dst + 1 * Lay::R1 * sizeof(S), &m1, bx1h, q0, bar);
-            tma_load_2d(dst + 2 * Lay::R1 * sizeof(S), &m1, bx1l, ne_r1 + q0, bar);
-            tma_load_2d(dst + 3 * Lay::R1 * sizeof(S), &m1, bx1h, ne_r1 + q0, bar);
+            tma_load_2d(dst + 0 * Lay::R1 * sizeof(S), mlp, bx1l, q0, bar);
+            tma_load_2d(dst + 1 * Lay::R1 * sizeof(S), m1p, bx1h, q0, bar);
+            tma_load_2d(dst + 2 * Lay::R1 * sizeof(S), m1p, bx1l, ne_r1 + q0, bar);
+            tma_load_2d(dst + 3 * Lay::R1 * sizeof(S), m1p, bx1h, ne_r1 + q0, bar);
         } else {
             if (l1) {
-                tma_load_2d(dst + 0 * Lay::R1 * sizeof(S), &m1, bx1h, q0, bar);
-                tma_load_2d(dst + 1 * Lay::R1 * sizeof(S), &m1, bx1l, ne_r1 + q0, bar);
-                tma_load_2d(dst + 2 * Lay::R1 * sizeof(S), &m1, bx1h, ne_r1 + q0, bar);
+                tma_load_2d(dst + 0 * Lay::R1 * sizeof(S), m1p, bx1h, q0, bar);
+                tma_load_2d(dst + 1 * Lay::R1 * sizeof(S), m1p, bx1l, ne_r1 + q0, bar);
+                tma_load_2d(dst + 2 * Lay::R1 * sizeof(S), m1p, bx1h, ne_r1 + q0, bar);
             }
             const uint32_t d2 = dst + 3 * Lay::R1 * sizeof(S);
             const int y2 = q0 / 2 + LAG;
-            tma_load_2d(d2 + 0 * Lay::R2 * sizeof(S), &ml, bx2l, y2, bar);
-            tma_load_2d(d2 + 1 * Lay::R2 * sizeof(S), &m2, bx2h, y2, bar);
-            tma_load_2d(d2 + 2 * Lay::R2 * sizeof(S), &m2, bx2l, ne_r2 + y2, bar);
-            tma_load_2d(d2 + 3 * Lay::R2 * sizeof(S), &m2, bx2h, ne_r2 + y2, bar);
+            tma_load_2d(d2 + 0 * Lay::R2 * sizeof(S), mlp, bx2l, y2, bar);
+            tma_load_2d(d2 + 1 * Lay::R2 * sizeof(S), m2p, bx2h, y2, bar);
+            tma_load_2d(d2 + 2 * Lay::R2 * sizeof(S), m2p, bx2l, ne_r2 + y2, bar);
+            tma_load_2d(d2 + 3 * Lay::R2 * sizeof(S), m2p, bx2h, ne_r2 + y2, bar);
         }
     };
     if (lane == 0) {
@@ -283,6 +280,37 @@ __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
         for (int t = s; t < nslots && t < s + kInvSlots; ++t)
             mbar_wait_bounded(bar_s + 8 * (t % kInvSlots), (t / kInvSlots) & 1, kWaitBudget);
     }
+}
+
+template <class S, int SCH, int NL, int Q1>
+__global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
+    inv_tma_kernel(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2,
+                   const __grid_constant__ CUtensorMap ml, const FusedArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int wid = blockIdx.x * kInvWarps + (threadIdx.x >> 5);
+    if (wid >= a.nstrips * a.nsegs) return;
+    inv_body<S, SCH, NL, Q1>(&m1, &m2, &ml, a, wid, smem_raw);
+}
+
+template <class S, int SCH, int NL, int Q1>
+__global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
+    inv_batched_kernel(const BatchEntry* __restrict__ table, int n) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int gw = blockIdx.x * kInvWarps + (threadIdx.x >> 5);
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (table[mid].first_warp <= gw) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchEntry& e = table[lo];
+    const int wid = gw - e.first_warp;
+    const FusedArgs a = e.args;  // registers: the body's stores cannot alias it
+    if (wid < 0 || wid >= a.nstrips * a.nsegs) return;
+    fence_tensormap_acquire(&e.m[0]);
+    fence_tensormap_acquire(&e.m[1]);
+    fence_tensormap_acquire(&e.m[2]);
+    inv_body<S, SCH, NL, Q1>(&e.m[0], &e.m[1], &e.m[2], a, wid, smem_raw);
 }
 
 size_t inv_tma_smem_bytes(int elem_bytes, int nl, int q1) {
@@ -332,6 +360,42 @@ static cudaError_t inv_launch_sch(int sch, int nl, int q1, const CUtensorMap& m1
         case SCH_SEP: return inv_launch_nl<T, SCH_SEP>(nl, q1, m1, m2, ml, a, grid, st);
         case SCH_NONSEP: return inv_launch_nl<T, SCH_NONSEP>(nl, q1, m1, m2, ml, a, grid, st);
         case SCH_RED: return inv_launch_nl<T, SCH_RED>(nl, q1, m1, m2, ml, a, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class S, int SCH, int NL>
+static cudaError_t inv_batched_one(const BatchEntry* table, int n, int grid, cudaStream_t st) {
+    auto k = inv_batched_kernel<S, SCH, NL, 2>;
+    const size_t smem = inv_tma_smem_bytes(sizeof(S), NL, 2);
+    if (grid == 0)
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, kInvWarps * 32, smem, st>>>(table, n);
+    return cudaGetLastError();
+}
+
+template <class S>
+static cudaError_t inv_batched_s(int sch, int nl, const BatchEntry* table, int n, int grid,
+                                 cudaStream_t st) {
+    if (nl < 1 || nl > 2) return cudaErrorInvalidValue;
+    switch (sch) {
+        case SCH_SEP: return nl == 1 ? inv_batched_one<S, SCH_SEP, 1>(table, n, grid, st)
+                                     : inv_batched_one<S, SCH_SEP, 2>(table, n, grid, st);
+        case SCH_NONSEP: return nl == 1 ? inv_batched_one<S, SCH_NONSEP, 1>(table, n, grid, st)
+                                        : inv_batched_one<S, SCH_NONSEP, 2>(table, n, grid, st);
+        case SCH_RED: return nl == 1 ? inv_batched_one<S, SCH_RED, 1>(table, n, grid, st)
+                                     : inv_batched_one<S, SCH_RED, 2>(table, n, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_inv_batched(int elem, int scheme, int nl, const BatchEntry* table, int n, int grid,
+                               cudaStream_t st) {
+    switch (elem) {
+        case 0: return inv_batched_s<float>(scheme, nl, table, n, grid, st);
+        case 1: return inv_batched_s<int>(scheme, nl, table, n, grid, st);
+        case 2: return inv_batched_s<__half>(scheme, nl, table, n, grid, st);
+        case 3: return inv_batched_s<__nv_bfloat16>(scheme, nl, table, n, grid, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -66,6 +66,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// A tensor map written to global memory by the host (a copy before the
+// launch) is read by the TMA unit through the tensor-map proxy: acquire it
+// there before the first copy that uses it.
+__device__ __forceinline__ void fence_tensormap_acquire(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(
+                     reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
 // About one second at GB300 clocks.
 constexpr long long kWaitBudget = 2000000000LL;
 

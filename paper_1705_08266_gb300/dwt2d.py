@@ -4,8 +4,8 @@ Every step of the transform runs in the library's CUDA kernels; PyTorch only
 provides device memory and streams.  The names follow the C ABI in
 include/dwt2d.h: Plan wraps dwt2d_plan, Plan.forward / Plan.inverse wrap
 dwt2d_forward / dwt2d_inverse, Plan.forward_host / inverse_host the host-buffer
-entry points.  There is no CPU fallback: if the library is missing the first
-call raises.
+entry points, Batch the dwt2d_batch_* calls.  There is no CPU fallback: if the
+library is missing the first call raises.
 """
 from __future__ import annotations
 
@@ -37,6 +37,20 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "alignment", -
 _lib = None
 
 
+class BatchItem(ctypes.Structure):
+    """dwt2d_batch_item."""
+    _fields_ = [("height", ctypes.c_int32), ("width", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("wavelet", ctypes.c_int), ("dtype", ctypes.c_int), ("inverse", ctypes.c_int32),
+                ("d_src", ctypes.c_void_p), ("src_pitch_bytes", ctypes.c_int64),
+                ("d_dst", ctypes.c_void_p), ("dst_pitch_bytes", ctypes.c_int64)]
+
+
+class Tuning(ctypes.Structure):
+    """dwt2d_tuning (0 = library default)."""
+    _fields_ = [("fuse_first", ctypes.c_int32), ("fuse_max", ctypes.c_int32),
+                ("warps_per_sm", ctypes.c_int32), ("min_segment", ctypes.c_int32)]
+
+
 class DwtError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -65,11 +79,19 @@ def lib() -> ctypes.CDLL:
     L.dwt2d_plan_set_launch_events.restype = ctypes.c_int
     L.dwt2d_plan_destroy.argtypes = [vp]
     L.dwt2d_plan_destroy.restype = None
+    L.dwt2d_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(BatchItem), i32, ctypes.c_int,
+                                     ctypes.POINTER(Tuning), ctypes.POINTER(sz)]
+    L.dwt2d_batch_upload.argtypes = [vp, vp, vp]
+    L.dwt2d_batch_launch.argtypes = [vp, vp, vp]
+    L.dwt2d_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
+    L.dwt2d_batch_destroy.argtypes = [vp]
+    L.dwt2d_batch_destroy.restype = None
     L.dwt2d_status_string.argtypes = [ctypes.c_int]
     L.dwt2d_status_string.restype = ctypes.c_char_p
     for name in ("dwt2d_plan", "dwt2d_forward", "dwt2d_inverse", "dwt2d_forward_host",
                  "dwt2d_inverse_host", "dwt2d_workspace_init", "dwt2d_workspace_status",
-                 "dwt2d_plan_info"):
+                 "dwt2d_plan_info", "dwt2d_batch_create", "dwt2d_batch_upload",
+                 "dwt2d_batch_launch", "dwt2d_batch_info"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -204,6 +226,66 @@ class Plan:
 
     def inverse_host(self, h_src, h_dst, d_in, d_out, workspace, scale=1.0, stream=None):
         return self._run_host("dwt2d_inverse_host", h_src, h_dst, d_in, d_out, workspace, scale, stream)
+
+
+class Batch:
+    """Many transforms in a few launches (dwt2d_batch_*).
+
+    jobs: sequence of (src, dst, levels, wavelet, inverse) with src / dst device
+    tensors of the same shape and dtype (16-byte-aligned rows; see empty_image).
+    The tensors are referenced, not copied: they must stay alive and in place
+    while the batch is used.  upload() writes the descriptor tables into the
+    workspace; launch() only launches kernels (capturable in a CUDA graph).
+    """
+
+    def __init__(self, jobs, scheme: str = "nonsep_reduced", tuning=None):
+        L = lib()
+        self.jobs = list(jobs)
+        self.scheme = scheme
+        arr = (BatchItem * max(1, len(self.jobs)))()
+        for i, (src, dst, levels, wavelet, inverse) in enumerate(self.jobs):
+            if src.shape != dst.shape or src.dtype != dst.dtype or src.dim() != 2:
+                raise ValueError("src and dst must be 2-D tensors of one shape and dtype")
+            es = src.element_size()
+            arr[i] = BatchItem(src.shape[0], src.shape[1], levels, WAVELETS[wavelet], DTYPES[src.dtype],
+                               int(bool(inverse)), src.data_ptr(), src.stride(0) * es, dst.data_ptr(),
+                               dst.stride(0) * es)
+        tun = None
+        if tuning is not None:
+            tun = ctypes.byref(Tuning(*[int(tuning.get(k, 0)) for k in
+                                        ("fuse_first", "fuse_max", "warps_per_sm", "min_segment")]))
+        self._h = ctypes.c_void_p()
+        ws = ctypes.c_size_t()
+        _check(L.dwt2d_batch_create(ctypes.byref(self._h), arr, len(self.jobs), SCHEMES[scheme], tun,
+                                    ctypes.byref(ws)), "dwt2d_batch_create")
+        self.workspace_bytes = ws.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.dwt2d_batch_destroy(h)
+            self._h = None
+
+    def info(self):
+        """(kernel launches per launch(), warp work items in all)."""
+        n, w = ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().dwt2d_batch_info(self._h, ctypes.byref(n), ctypes.byref(w)), "batch_info")
+        return n.value, w.value
+
+    def workspace(self, device="cuda") -> torch.Tensor:
+        # 256-byte aligned (the caching allocator's blocks are)
+        return torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=device)
+
+    def upload(self, workspace: torch.Tensor, stream=None):
+        _check(lib().dwt2d_batch_upload(self._h, ctypes.c_void_p(workspace.data_ptr()),
+                                        _stream_ptr(stream)), "dwt2d_batch_upload")
+
+    def launch(self, workspace: torch.Tensor, stream=None):
+        _check(lib().dwt2d_batch_launch(self._h, ctypes.c_void_p(workspace.data_ptr()),
+                                        _stream_ptr(stream)), "dwt2d_batch_launch")
+
+    def status(self, workspace: torch.Tensor, stream=None) -> int:
+        return lib().dwt2d_workspace_status(ctypes.c_void_p(workspace.data_ptr()), _stream_ptr(stream))
 
 
 def forward(x: torch.Tensor, levels: int, wavelet: str = "cdf97", scheme: str = "nonsep_reduced"):

@@ -91,3 +91,62 @@ def test_bad_pointers_rejected_without_gpu(L):
 def test_status_strings(L):
     for s in (0, -1, -2, -3, -4, -5, -6):
         assert L.dwt2d_status_string(s)
+
+
+def _item(h, w, lv, wav=0, dt=0, inv=0, src=1 << 20, dst=2 << 20, sp=None, dp=None):
+    es = 2 if dt in (2, 3) else 4
+    pitch = (w * es + 15) // 16 * 16
+    return D.BatchItem(h, w, lv, wav, dt, inv, src, sp if sp is not None else pitch, dst,
+                       dp if dp is not None else pitch)
+
+
+def _batch(L, items, scheme=2, tuning=None):
+    arr = (D.BatchItem * max(1, len(items)))(*items)
+    b = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    t = ctypes.byref(tuning) if tuning is not None else None
+    st = L.dwt2d_batch_create(ctypes.byref(b), arr, len(items), scheme, t, ctypes.byref(ws))
+    return st, b, ws.value
+
+
+def test_batch_planning_launch_list(L):
+    """Phases x (direction, storage, fusion depth) buckets; placeholder pointers
+    (nothing is touched before upload)."""
+    items = [_item(64, 64, 3), _item(100, 37, 1), _item(64, 64, 2, wav=1, dt=1),
+             _item(64, 64, 3, inv=1), _item(64, 48, 2, dt=2)]
+    st, b, ws = _batch(L, items)
+    assert st == 0 and ws > 256
+    n, w = ctypes.c_int32(), ctypes.c_int64()
+    assert L.dwt2d_batch_info(b, ctypes.byref(n), ctypes.byref(w)) == 0
+    # phase 0: fwd f32 nl1 (the 1-level item), fwd f32 nl2, fwd i32 nl2, fwd f16 nl2,
+    #          inv f32 nl1 (the 3-level inverse runs its 1-level coarse group first)
+    # phase 1: fwd f32 nl1 (the 3-level item), inv f32 nl2
+    assert n.value == 7
+    assert w.value >= len(items)
+    L.dwt2d_batch_destroy(b)
+
+
+@pytest.mark.parametrize("case,status", [
+    ("multipass_scheme", -2), ("fuse3", -2), ("same_buffer", -1), ("bad_pitch", -3),
+    ("bad_levels", -1), ("int_cdf", -2), ("empty", 0)])
+def test_batch_validation(L, case, status):
+    items = [_item(64, 64, 2)]
+    scheme, tun = 2, None
+    if case == "multipass_scheme":
+        scheme = 3
+    elif case == "fuse3":
+        tun = D.Tuning(0, 3, 0, 0)
+    elif case == "same_buffer":
+        items = [_item(64, 64, 2, dst=1 << 20)]
+    elif case == "bad_pitch":
+        items = [_item(64, 64, 2, sp=264)]
+    elif case == "bad_levels":
+        items = [_item(64, 64, 0)]
+    elif case == "int_cdf":
+        items = [_item(64, 64, 2, wav=0, dt=1)]
+    elif case == "empty":
+        items = []
+    st, b, ws = _batch(L, items, scheme, tun)
+    assert st == status
+    if st == 0:
+        L.dwt2d_batch_destroy(b)

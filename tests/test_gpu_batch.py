@@ -1,0 +1,201 @@
+"""Batched transforms: many images of different sizes, level counts, wavelets,
+storage types and directions in a few launches.
+
+Each image of a batch must come out bit for bit as the single-image entry
+point computes it (same lifting arithmetic, only the warp-to-work mapping
+differs), and within the oracle's tolerance.  A batch captured in a CUDA graph
+and replayed on new input contents gives the same results again.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import lifting as L
+from paper_1705_08266_gb300 import dwt2d as D
+from paper_1705_08266_gb300 import synth
+from tests.parity_util import TOL_F32, assert_forward_matches, device_image
+
+pytestmark = pytest.mark.gpu
+
+# (height, width, levels, wavelet, dtype, inverse)
+MIXED = [
+    (96, 130, 3, "cdf97", torch.float32, 0),
+    (1, 5, 1, "cdf97", torch.float32, 0),
+    (3, 3, 2, "cdf97", torch.float32, 1),
+    (257, 511, 5, "cdf97", torch.float32, 0),
+    (64, 64, 1, "cdf97", torch.float32, 1),
+    (200, 33, 4, "legall53", torch.int32, 0),
+    (130, 96, 3, "legall53", torch.int32, 1),
+    (77, 1030, 2, "cdf97", torch.float16, 0),
+    (512, 300, 6, "cdf97", torch.bfloat16, 1),
+    (1030, 770, 5, "cdf97", torch.float32, 1),
+    (17, 2, 3, "legall53", torch.int32, 0),
+    (640, 480, 3, "cdf97", torch.float32, 0),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    D.lib()
+
+
+def _input(h, w, levels, wavelet, dtype, inverse, seed):
+    """The host array a job starts from (image, or coefficients of one)."""
+    x = synth.image(wavelet, h, w, seed)
+    if dtype in (torch.float16, torch.bfloat16):
+        x = (x / max(1.0, float(np.max(np.abs(x))))).astype(np.float32)
+    if inverse:
+        c = L.forward(x.astype(np.int64 if wavelet == "legall53" else np.float64), levels, wavelet)
+        x = c.astype(np.int32) if wavelet == "legall53" else c.astype(np.float32)
+    return torch.from_numpy(x).to(dtype)
+
+
+def _jobs(spec, seed0, scheme="nonsep_reduced"):
+    jobs, hosts = [], []
+    for i, (h, w, lv, wav, dt, inv) in enumerate(spec):
+        xh = _input(h, w, lv, wav, dt, inv, seed0 + i)
+        src = D.empty_image(h, w, dt)
+        src.copy_(xh)
+        dst = D.empty_image(h, w, dt)
+        dst.fill_(0)
+        jobs.append((src, dst, lv, wav, inv))
+        hosts.append(xh)
+    return jobs, hosts
+
+
+def _single(src, levels, wavelet, inverse, scheme):
+    plan = D.Plan(src.shape[0], src.shape[1], levels, wavelet, scheme, src.dtype)
+    out = plan.inverse(src) if inverse else plan.forward(src)
+    return out
+
+
+def _assert_same_as_single(jobs, scheme, what):
+    for i, (src, dst, lv, wav, inv) in enumerate(jobs):
+        ref = _single(src, lv, wav, inv, scheme)
+        torch.cuda.synchronize()
+        a, b = dst.cpu(), ref.cpu()
+        if not torch.equal(a, b):
+            d = (a.to(torch.float64) - b.to(torch.float64)).abs().max().item()
+            raise AssertionError(f"{what} item {i} {tuple(src.shape)} L{lv} {wav} inv={inv}: "
+                                 f"differs from the single-image call, max |diff| {d:.3g}")
+
+
+@pytest.mark.parametrize("scheme", ["nonsep_reduced", "separable", "nonsep"])
+def test_mixed_batch_equals_single_image_calls(scheme):
+    jobs, hosts = _jobs(MIXED, 2026, scheme)
+    batch = D.Batch(jobs, scheme)
+    ws = batch.workspace()
+    batch.upload(ws)
+    batch.launch(ws)
+    torch.cuda.synchronize()
+    assert batch.status(ws) == 0
+    launches, warps = batch.info()
+    assert 1 <= launches <= 3 * 2 * 4 * 2  # phases x directions x types x depths
+    _assert_same_as_single(jobs, scheme, scheme)
+
+
+def test_mixed_batch_against_oracle():
+    jobs, hosts = _jobs(MIXED, 4242)
+    batch = D.Batch(jobs)
+    ws = batch.workspace()
+    batch.upload(ws)
+    batch.launch(ws)
+    torch.cuda.synchronize()
+    for (src, dst, lv, wav, inv), xh in zip(jobs, hosts):
+        if xh.dtype in (torch.float16, torch.bfloat16):
+            continue  # 16-bit storage has its own tolerance tests
+        got = dst.cpu().numpy()
+        if inv:
+            ref = L.inverse(xh.numpy().astype(np.float64) if wav == "cdf97" else xh.numpy().astype(np.int64),
+                            lv, wav)
+            if wav == "legall53":
+                assert np.array_equal(got.astype(np.int64), ref)
+            else:
+                maxabs = float(np.max(np.abs(ref)))
+                assert float(np.max(np.abs(got - ref))) <= TOL_F32 * max(maxabs, 1.0) * lv
+        else:
+            assert_forward_matches(got, xh.numpy(), lv, wav, f"{tuple(xh.shape)} L{lv}")
+
+
+def test_many_small_images_one_launch_per_bucket():
+    rng = np.random.default_rng(1705)
+    spec = []
+    for _ in range(256):
+        h, w = int(rng.integers(16, 300)), int(rng.integers(16, 300))
+        spec.append((h, w, 3, "cdf97", torch.float32, 0))
+    jobs, _ = _jobs(spec, 7000)
+    batch = D.Batch(jobs)
+    launches, warps = batch.info()
+    assert launches == 2  # phase 0: 2 fused levels, phase 1: the last level
+    assert warps >= 256
+    ws = batch.workspace()
+    batch.upload(ws)
+    batch.launch(ws)
+    torch.cuda.synchronize()
+    assert batch.status(ws) == 0
+    _assert_same_as_single(jobs, "nonsep_reduced", "256 images")
+
+
+@pytest.mark.parametrize("tuning", [{"fuse_first": 1, "fuse_max": 1}, {"warps_per_sm": 2},
+                                    {"min_segment": 64}, {"fuse_first": 2, "warps_per_sm": 40}])
+def test_tuning_knobs_keep_results(tuning):
+    """Different fusion depths and decompositions: the same coefficients (the
+    oracle's, within tolerance; bit-exact where only the decomposition moves)."""
+    jobs, hosts = _jobs(MIXED[:6], 99)
+    batch = D.Batch(jobs, tuning=tuning)
+    ws = batch.workspace()
+    batch.upload(ws)
+    batch.launch(ws)
+    torch.cuda.synchronize()
+    assert batch.status(ws) == 0
+    if "fuse_first" in tuning and tuning.get("fuse_max", 2) == 1:
+        for (src, dst, lv, wav, inv), xh in zip(jobs, hosts):
+            if not inv:
+                assert_forward_matches(dst.cpu().numpy(), xh.numpy(), lv, wav, str(tuning))
+    else:
+        _assert_same_as_single(jobs, "nonsep_reduced", str(tuning))
+
+
+def test_cuda_graph_replay_on_new_inputs():
+    jobs, _ = _jobs(MIXED, 31)
+    batch = D.Batch(jobs)
+    ws = batch.workspace()
+    side = torch.cuda.Stream()
+    batch.upload(ws, stream=side)
+    side.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        batch.launch(ws, stream=side)
+    for seed in (5, 6):
+        for i, (src, dst, lv, wav, inv) in enumerate(jobs):
+            h, w = src.shape
+            src.copy_(_input(h, w, lv, wav, src.dtype, inv, seed * 100 + i))
+            dst.fill_(0)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert batch.status(ws) == 0
+        _assert_same_as_single(jobs, "nonsep_reduced", f"graph replay {seed}")
+
+
+def test_single_item_batch_and_round_trip():
+    x = synth.image("cdf97", 1030, 2050, 8)
+    src = device_image(x)
+    mid = D.empty_image(1030, 2050)
+    out = D.empty_image(1030, 2050)
+    b1 = D.Batch([(src, mid, 5, "cdf97", 0)])
+    ws1 = b1.workspace()
+    b1.upload(ws1)
+    b1.launch(ws1)
+    b2 = D.Batch([(mid, out, 5, "cdf97", 1)])
+    ws2 = b2.workspace()
+    b2.upload(ws2)
+    b2.launch(ws2)
+    torch.cuda.synchronize()
+    ref = D.Plan(1030, 2050, 5).forward(src)
+    torch.cuda.synchronize()
+    assert torch.equal(mid.cpu(), ref.cpu())
+    maxabs = float(np.max(np.abs(x)))
+    assert float(np.max(np.abs(out.cpu().numpy() - x))) <= 2 * 5 * TOL_F32 * maxabs
