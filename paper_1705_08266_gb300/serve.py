@@ -1,0 +1,388 @@
+"""Serving loop: continuous batching of transform requests under a device
+memory budget.
+
+Requests (an image to transform forward, or Mallat coefficients to transform
+back) are queued as they arrive.  Each call of Server.poll() retires the
+batches whose kernels have finished and admits queued requests, in arrival
+order, while their device memory fits the budget, into one new batch
+(dwt2d_batch_*: a few kernel launches for any mix of sizes, level counts,
+wavelets, storage types and directions).  Several batches may be in flight on
+the stream at once, so the host prepares the next batch while the GPU runs the
+previous one.
+
+Memory: a request reserves its output (kept resident on the device until the
+client calls release()), its share of the batch workspace, and a device copy of
+its input when the input is on the host or not pitched for the kernels.  A
+request that can never fit is rejected at submit; the others wait (back
+pressure) until earlier results are released.
+
+Failures stay with the request that caused them: a malformed request is
+rejected at submit, a refused allocation fails that request only, a cancelled
+request is dropped (or its result discarded), and a slow input loader runs on a
+worker thread while the queue moves on.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import itertools
+import threading
+import time
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional
+
+import torch
+
+QUEUED, LOADING, RUNNING, DONE, FAILED, CANCELLED, REJECTED = (
+    "queued", "loading", "running", "done", "failed", "cancelled", "rejected")
+
+VALID_TYPES = {("cdf97", torch.float32), ("cdf97", torch.float16), ("cdf97", torch.bfloat16),
+               ("legall53", torch.int32)}
+TABLE_ENTRY_BYTES = 1024  # descriptor table bytes reserved per request and launch
+
+
+@dataclass
+class Request:
+    """One transform: `data` (H, W) on the host or the device, or a `loader`
+    that returns it (run on a worker thread)."""
+    height: int
+    width: int
+    levels: int
+    wavelet: str = "cdf97"
+    dtype: torch.dtype = torch.float32
+    inverse: bool = False
+    data: Optional[torch.Tensor] = None
+    loader: Optional[Callable[[], torch.Tensor]] = None
+
+
+@dataclass
+class Ticket:
+    id: int
+    request: Request
+    state: str = QUEUED
+    error: str = ""
+    result: Optional[torch.Tensor] = None
+    t_submit: float = 0.0
+    t_start: float = 0.0
+    t_done: float = 0.0
+    reserved: int = 0          # bytes counted against the budget
+    reserved_out: int = 0      # the part that stays resident with the result
+    _src: Optional[torch.Tensor] = field(default=None, repr=False)
+    _event: threading.Event = field(default_factory=threading.Event, repr=False)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_submit
+
+    def finished(self) -> bool:
+        return self.state in (DONE, FAILED, CANCELLED, REJECTED)
+
+
+def validate(req: Request) -> str:
+    """'' if the request is well formed, else the reason."""
+    if not isinstance(req, Request):
+        return "not a Request"
+    for name in ("height", "width", "levels"):
+        if not isinstance(getattr(req, name), int):
+            return f"{name} must be an int"
+    if not (1 <= req.height <= 65536 and 1 <= req.width <= 65536):
+        return "height and width must be in 1..65536"
+    if not 1 <= req.levels <= 16:
+        return "levels must be in 1..16"
+    if (req.wavelet, req.dtype) not in VALID_TYPES:
+        return f"unsupported wavelet / storage type {req.wavelet} / {req.dtype}"
+    if (req.data is None) == (req.loader is None):
+        return "exactly one of data and loader is needed"
+    if req.data is not None:
+        return check_data(req, req.data)
+    return ""
+
+
+def check_data(req: Request, t) -> str:
+    if not isinstance(t, torch.Tensor):
+        return "data is not a tensor"
+    if t.dim() != 2 or tuple(t.shape) != (req.height, req.width):
+        return f"data shape {tuple(t.shape)} != ({req.height}, {req.width})"
+    if t.dtype != req.dtype:
+        return f"data dtype {t.dtype} != {req.dtype}"
+    return ""
+
+
+class GpuExecutor:
+    """Runs a batch with the library's batched kernels on one stream."""
+
+    def __init__(self, device="cuda", scheme="nonsep_reduced", tuning=None, stream=None):
+        from . import dwt2d as D
+
+        self.D = D
+        self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.scheme = scheme
+        self.tuning = tuning
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+
+    def workspace_bytes(self, req: Request) -> int:
+        plan = self.D.Plan(req.height, req.width, req.levels, req.wavelet, self.scheme, req.dtype)
+        return plan.workspace_bytes
+
+    def empty(self, h, w, dtype):
+        with torch.cuda.stream(self.stream):  # blocks owned by the serving stream
+            return self.D.empty_image(h, w, dtype, self.device)
+
+    def pitched(self, t: torch.Tensor) -> bool:
+        es = t.element_size()
+        return (t.device == self.device and t.stride(1) == 1 and (t.stride(0) * es) % 16 == 0
+                and t.data_ptr() % 16 == 0)
+
+    def copy_in(self, dst: torch.Tensor, src: torch.Tensor):
+        with torch.cuda.stream(self.stream):
+            dst.copy_(src, non_blocking=True)
+
+    def launch(self, jobs):
+        batch = self.D.Batch(jobs, self.scheme, self.tuning)
+        with torch.cuda.stream(self.stream):
+            ws = batch.workspace(self.device)
+        batch.upload(ws, stream=self.stream)
+        batch.launch(ws, stream=self.stream)
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        return (batch, ws, ev)
+
+    def done(self, handle) -> bool:
+        return handle[2].query()
+
+    def status(self, handle) -> int:
+        batch, ws, _ = handle
+        return batch.status(ws, stream=self.stream)
+
+
+class Server:
+    """Continuous batching under `budget_bytes` of device memory."""
+
+    def __init__(self, budget_bytes: int = 40 << 30, executor=None, max_batch: int = 256,
+                 max_inflight: int = 4, allocator: Optional[Callable] = None, loader_threads: int = 4,
+                 clock: Callable[[], float] = time.perf_counter, **executor_args):
+        self.budget = int(budget_bytes)
+        self.ex = executor if executor is not None else GpuExecutor(**executor_args)
+        self.max_batch = max_batch
+        self.max_inflight = max_inflight
+        self.alloc = allocator if allocator is not None else (lambda t, h, w, dt: self.ex.empty(h, w, dt))
+        self.clock = clock
+        self.in_use = 0
+        self.peak = 0
+        self.queue: List[Ticket] = []
+        self.inflight = []  # (handle, [tickets])
+        self.tickets = {}
+        self.finished: List[Ticket] = []
+        self._ids = itertools.count()
+        self._lock = threading.Lock()
+        self._loaders = cf.ThreadPoolExecutor(max_workers=loader_threads)
+        self._loading = 0
+        self.batches = 0
+
+    # ---- client side
+    def submit(self, req: Request, t_arrival: Optional[float] = None) -> Ticket:
+        """Queue a request (latency counts from t_arrival, default now)."""
+        t = Ticket(next(self._ids), req, t_submit=self.clock() if t_arrival is None else t_arrival)
+        self.tickets[t.id] = t
+        why = validate(req)
+        if not why:
+            try:
+                t.reserved_out, tmp = self._need(req)
+                t.reserved = t.reserved_out + tmp
+            except Exception as e:  # a plan the library refuses
+                why = f"plan refused: {e}"
+        if not why and t.reserved > self.budget:
+            why = f"needs {t.reserved} bytes, budget {self.budget}"
+        if why:
+            self._finish(t, REJECTED, why)
+            return t
+        if req.loader is not None:
+            t.state = LOADING
+            with self._lock:
+                self._loading += 1
+            self._loaders.submit(self._load, t)
+        else:
+            t._src = req.data
+            with self._lock:
+                self.queue.append(t)
+        return t
+
+    def cancel(self, t: Ticket) -> bool:
+        """Drop a request that has not finished; its result (if the kernels are
+        already running) is discarded when they end."""
+        with self._lock:
+            if t.finished():
+                return False
+            if t in self.queue:
+                self.queue.remove(t)
+            if t.state == RUNNING:
+                t.state = CANCELLED  # retire() releases its memory
+                t.error = "cancelled while running"
+                return True
+        self._finish(t, CANCELLED, "cancelled")
+        return True
+
+    def release(self, t: Ticket) -> None:
+        """The client is done with a resident result: return its memory."""
+        if t.result is not None:
+            t.result = None
+            self._unreserve(t)
+
+    def poll(self) -> int:
+        """Retire finished batches, then admit and launch one new batch.
+        Returns the number of requests that finished in this call."""
+        n = self.retire()
+        if len(self.inflight) < self.max_inflight:
+            self.admit_and_launch()
+        return n
+
+    def run_until_idle(self, timeout: float = 60.0, sleep: float = 0.0) -> bool:
+        t_end = self.clock() + timeout
+        while self.clock() < t_end:
+            self.poll()
+            with self._lock:
+                busy = self.queue or self.inflight or self._loading
+            if not busy:
+                return True
+            if sleep:
+                time.sleep(sleep)
+        return False
+
+    def stats(self) -> dict:
+        done = [t for t in self.finished if t.state == DONE]
+        lat = sorted(t.latency for t in done)
+
+        def q(p):
+            if not lat:
+                return None
+            return lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))]
+
+        count = {s: 0 for s in (DONE, FAILED, CANCELLED, REJECTED)}
+        for t in self.finished:
+            count[t.state] = count.get(t.state, 0) + 1
+        return {"completed": count[DONE], "failed": count[FAILED], "cancelled": count[CANCELLED],
+                "rejected": count[REJECTED], "p50_s": q(0.50), "p99_s": q(0.99),
+                "max_s": lat[-1] if lat else None, "batches": self.batches,
+                "peak_bytes": self.peak, "budget_bytes": self.budget}
+
+    def close(self):
+        self._loaders.shutdown(wait=True)
+
+    # ---- internals
+    def _need(self, req: Request):
+        """(resident output bytes, bytes held only while the kernels run)."""
+        es = torch.empty((), dtype=req.dtype).element_size()
+        img = req.height * ((req.width * es + 15) // 16 * 16)
+        tmp = self.ex.workspace_bytes(req) + 4 * TABLE_ENTRY_BYTES
+        data = req.data
+        if data is None or not self.ex.pitched(data):
+            tmp += img  # device copy of the input
+        return img, tmp
+
+    def _load(self, t: Ticket):
+        try:
+            data = t.request.loader()
+            why = check_data(t.request, data)
+        except Exception as e:  # the loader's own failure
+            data, why = None, f"loader failed: {e!r}"
+        with self._lock:
+            self._loading -= 1
+            if t.state != LOADING:  # cancelled meanwhile
+                return
+            if why:
+                t.state = FAILED
+            else:
+                t._src = data
+                t.state = QUEUED
+                self.queue.append(t)
+        if why:
+            self._finish(t, FAILED, why)
+
+    def _reserve(self, n: int):
+        self.in_use += n
+        self.peak = max(self.peak, self.in_use)
+
+    def _unreserve(self, t: Ticket, keep_out: bool = False):
+        with self._lock:
+            keep = t.reserved_out if keep_out else 0
+            self.in_use -= t.reserved - keep
+            t.reserved = keep
+
+    def _finish(self, t: Ticket, state: str, error: str = ""):
+        t.state = state
+        t.error = error
+        t.t_done = self.clock()
+        if state != DONE:
+            t.result = None
+            t._src = None
+        self.finished.append(t)
+        t._event.set()
+
+    def admit_and_launch(self):
+        picked = []
+        with self._lock:
+            for t in self.queue:
+                # arrival order: nobody overtakes a request waiting for memory
+                if len(picked) == self.max_batch or self.in_use + t.reserved > self.budget:
+                    break
+                self._reserve(t.reserved)
+                picked.append(t)
+            self.queue = self.queue[len(picked):]
+        if not picked:
+            return
+        jobs, ok = [], []
+        for t in picked:
+            r = t.request
+            try:
+                src = t._src
+                if not self.ex.pitched(src):
+                    dev = self.alloc(t, r.height, r.width, r.dtype)
+                    self.ex.copy_in(dev, src)
+                    src = dev
+                out = self.alloc(t, r.height, r.width, r.dtype)
+            except Exception as e:  # allocation refused: this request only
+                self._unreserve(t)
+                self._finish(t, FAILED, f"allocation refused: {e!r}")
+                continue
+            t._src = src
+            t.result = out
+            t.state = RUNNING
+            t.t_start = self.clock()
+            jobs.append((src, out, r.levels, r.wavelet, int(r.inverse)))
+            ok.append(t)
+        if not ok:
+            return
+        try:
+            handle = self.ex.launch(jobs)
+        except Exception as e:
+            for t in ok:
+                self._unreserve(t)
+                self._finish(t, FAILED, f"launch failed: {e!r}")
+            return
+        self.batches += 1
+        self.inflight.append((handle, ok))
+
+    def retire(self) -> int:
+        n = 0
+        still = []
+        for handle, tickets in self.inflight:
+            if not self.ex.done(handle):
+                still.append((handle, tickets))
+                continue
+            status = self.ex.status(handle)
+            for t in tickets:
+                t._src = None
+                if t.state == CANCELLED:
+                    t.result = None
+                    self._unreserve(t)
+                    self._finish(t, CANCELLED, t.error)
+                elif status != 0:
+                    self._unreserve(t)
+                    self._finish(t, FAILED, f"kernel status {status}")
+                else:
+                    self._unreserve(t, keep_out=True)  # the output stays resident
+                    self._finish(t, DONE)
+                n += 1
+        self.inflight = still
+        return n
