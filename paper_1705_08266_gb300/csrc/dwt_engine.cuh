@@ -214,6 +214,15 @@ __device__ __forceinline__ void copy_arr(T (&d)[Q], const T (&s)[Q]) {
     for (int j = 0; j < Q; ++j) d[j] = s[j];
 }
 
+// Two adjacent columns of a lane as one packed pair, and back.
+template <int Q>
+__device__ __forceinline__ float2 pk(const float (&v)[Q], int j) { return make_float2(v[j], v[j + 1]); }
+template <int Q>
+__device__ __forceinline__ void unpk(float2 p, float (&v)[Q], int j) {
+    v[j] = p.x;
+    v[j + 1] = p.y;
+}
+
 enum Kind { K_NONE = 0, K_DOWN = 1, K_UP = 2 };
 
 // ------------------------------------------------------------------ ops ----
@@ -243,7 +252,7 @@ template <bool EDGE>
 __device__ __forceinline__ bool vact(const LevelCtx& x) { return EDGE ? x.va : true; }
 
 // float, separable (Sec. 2 matrices)
-template <int ID, int SIGN>
+template <int ID, int SIGN, bool PACK>
 struct OpFTH {
     static constexpr int kind = K_NONE;
     template <bool EDGE, int Q>
@@ -252,22 +261,42 @@ struct OpFTH {
         right_nb<EDGE>(a.c[0], c0r, x.right);
         right_nb<EDGE>(a.c[2], c2r, x.right);
         const float p = hcoef<EDGE>(Coef<ID, SIGN>::v, x);
+        if constexpr (PACK && Q % 2 == 0) {
 #pragma unroll
-        for (int j = 0; j < Q; ++j) f_TH(a.c[1][j], a.c[3][j], a.c[0][j], c0r[j], a.c[2][j], c2r[j], p);
+            for (int j = 0; j < Q; j += 2) {
+                float2 c1 = pk(a.c[1], j), c3 = pk(a.c[3], j);
+                f_TH(c1, c3, pk(a.c[0], j), pk(c0r, j), pk(a.c[2], j), pk(c2r, j), p);
+                unpk(c1, a.c[1], j);
+                unpk(c3, a.c[3], j);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) f_TH(a.c[1][j], a.c[3][j], a.c[0][j], c0r[j], a.c[2][j], c2r[j], p);
+        }
     }
 };
-template <int ID, int SIGN>
+template <int ID, int SIGN, bool PACK>
 struct OpFTV {
     static constexpr int kind = K_DOWN;
     template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<float, Q>& a, const float (&n0)[Q],
                                                  const float (&n1)[Q], const LevelCtx& x) {
         const float p = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
+        if constexpr (PACK && Q % 2 == 0) {
 #pragma unroll
-        for (int j = 0; j < Q; ++j) f_TV(a.c[2][j], a.c[3][j], a.c[0][j], n0[j], a.c[1][j], n1[j], p);
+            for (int j = 0; j < Q; j += 2) {
+                float2 c2 = pk(a.c[2], j), c3 = pk(a.c[3], j);
+                f_TV(c2, c3, pk(a.c[0], j), pk(n0, j), pk(a.c[1], j), pk(n1, j), p);
+                unpk(c2, a.c[2], j);
+                unpk(c3, a.c[3], j);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) f_TV(a.c[2][j], a.c[3][j], a.c[0][j], n0[j], a.c[1][j], n1[j], p);
+        }
     }
 };
-template <int ID, int SIGN>
+template <int ID, int SIGN, bool PACK>
 struct OpFSH {
     static constexpr int kind = K_NONE;
     template <bool EDGE, int Q>
@@ -280,11 +309,21 @@ struct OpFSH {
         left_nb<EDGE>(a.c[1], c1l, x.left);
         left_nb<EDGE>(a.c[3], c3l, x.left);
         const float u = hcoef<EDGE>(Coef<ID, SIGN>::v, x);
+        if constexpr (PACK && Q % 2 == 0) {
 #pragma unroll
-        for (int j = 0; j < Q; ++j) f_SH(a.c[0][j], a.c[2][j], a.c[1][j], c1l[j], a.c[3][j], c3l[j], u);
+            for (int j = 0; j < Q; j += 2) {
+                float2 c0 = pk(a.c[0], j), c2 = pk(a.c[2], j);
+                f_SH(c0, c2, pk(a.c[1], j), pk(c1l, j), pk(a.c[3], j), pk(c3l, j), u);
+                unpk(c0, a.c[0], j);
+                unpk(c2, a.c[2], j);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) f_SH(a.c[0][j], a.c[2][j], a.c[1][j], c1l[j], a.c[3][j], c3l[j], u);
+        }
     }
 };
-template <int ID, int SIGN>
+template <int ID, int SIGN, bool PACK>
 struct OpFSV {
     static constexpr int kind = K_UP;
     static constexpr bool kHsub = false;
@@ -292,13 +331,23 @@ struct OpFSV {
     __device__ __forceinline__ static void apply(Quads<float, Q>& a, const float (&up2)[Q],
                                                  const float (&up3)[Q], const LevelCtx& x) {
         const float u = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
+        if constexpr (PACK && Q % 2 == 0) {
 #pragma unroll
-        for (int j = 0; j < Q; ++j) f_SV(a.c[0][j], a.c[1][j], a.c[2][j], up2[j], a.c[3][j], up3[j], u);
+            for (int j = 0; j < Q; j += 2) {
+                float2 c0 = pk(a.c[0], j), c1 = pk(a.c[1], j);
+                f_SV(c0, c1, pk(a.c[2], j), pk(up2, j), pk(a.c[3], j), pk(up3, j), u);
+                unpk(c0, a.c[0], j);
+                unpk(c1, a.c[1], j);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) f_SV(a.c[0][j], a.c[1][j], a.c[2][j], up2[j], a.c[3][j], up3[j], u);
+        }
     }
 };
 
 // float, non-separable (Sec. 3; RED = reduced form)
-template <int ID, int SIGN, bool RED>
+template <int ID, int SIGN, bool RED, bool PACK>
 struct OpFT {
     static constexpr int kind = K_DOWN;
     template <bool EDGE, int Q>
@@ -309,18 +358,34 @@ struct OpFT {
         right_nb<EDGE>(a.c[2], c2r, x.right);
         right_nb<EDGE>(n0, n0r, x.right);
         const float ph = hcoef<EDGE>(Coef<ID, SIGN>::v, x), pv = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
+        if constexpr (PACK && Q % 2 == 0) {
 #pragma unroll
-        for (int j = 0; j < Q; ++j) {
-            if (RED)
-                f_T_red(a.c[1][j], a.c[2][j], a.c[3][j], a.c[0][j], c0r[j], c2r[j], n0[j], n1[j],
-                        n0r[j], ph, pv);
-            else
-                f_T_plain(a.c[1][j], a.c[2][j], a.c[3][j], a.c[0][j], c0r[j], c2r[j], n0[j], n1[j],
-                          n0r[j], ph, pv);
+            for (int j = 0; j < Q; j += 2) {
+                float2 c1 = pk(a.c[1], j), c2 = pk(a.c[2], j), c3 = pk(a.c[3], j);
+                if (RED)
+                    f_T_red(c1, c2, c3, pk(a.c[0], j), pk(c0r, j), pk(c2r, j), pk(n0, j), pk(n1, j),
+                            pk(n0r, j), ph, pv);
+                else
+                    f_T_plain(c1, c2, c3, pk(a.c[0], j), pk(c0r, j), pk(c2r, j), pk(n0, j), pk(n1, j),
+                              pk(n0r, j), ph, pv);
+                unpk(c1, a.c[1], j);
+                unpk(c2, a.c[2], j);
+                unpk(c3, a.c[3], j);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                if (RED)
+                    f_T_red(a.c[1][j], a.c[2][j], a.c[3][j], a.c[0][j], c0r[j], c2r[j], n0[j], n1[j],
+                            n0r[j], ph, pv);
+                else
+                    f_T_plain(a.c[1][j], a.c[2][j], a.c[3][j], a.c[0][j], c0r[j], c2r[j], n0[j], n1[j],
+                              n0r[j], ph, pv);
+            }
         }
     }
 };
-template <int ID, int SIGN, bool RED>
+template <int ID, int SIGN, bool RED, bool PACK>
 struct OpFS {
     static constexpr int kind = K_UP;
     static constexpr bool kHsub = true;
@@ -332,14 +397,30 @@ struct OpFS {
         left_nb<EDGE>(a.c[3], c3l, x.left);
         left_nb<EDGE>(up3, u3l, x.left);
         const float uh = hcoef<EDGE>(Coef<ID, SIGN>::v, x), uv = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
+        if constexpr (PACK && Q % 2 == 0) {
 #pragma unroll
-        for (int j = 0; j < Q; ++j) {
-            if (RED)
-                f_S_red(a.c[0][j], a.c[1][j], a.c[2][j], a.c[3][j], c1l[j], c3l[j], up2[j], up3[j],
-                        u3l[j], uh, uv);
-            else
-                f_S_plain(a.c[0][j], a.c[1][j], a.c[2][j], a.c[3][j], c1l[j], c3l[j], up2[j],
-                          up3[j], u3l[j], uh, uv);
+            for (int j = 0; j < Q; j += 2) {
+                float2 c0 = pk(a.c[0], j), c1 = pk(a.c[1], j), c2 = pk(a.c[2], j);
+                if (RED)
+                    f_S_red(c0, c1, c2, pk(a.c[3], j), pk(c1l, j), pk(c3l, j), pk(up2, j), pk(up3, j),
+                            pk(u3l, j), uh, uv);
+                else
+                    f_S_plain(c0, c1, c2, pk(a.c[3], j), pk(c1l, j), pk(c3l, j), pk(up2, j),
+                              pk(up3, j), pk(u3l, j), uh, uv);
+                unpk(c0, a.c[0], j);
+                unpk(c1, a.c[1], j);
+                unpk(c2, a.c[2], j);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                if (RED)
+                    f_S_red(a.c[0][j], a.c[1][j], a.c[2][j], a.c[3][j], c1l[j], c3l[j], up2[j],
+                            up3[j], u3l[j], uh, uv);
+                else
+                    f_S_plain(a.c[0][j], a.c[1][j], a.c[2][j], a.c[3][j], c1l[j], c3l[j], up2[j],
+                              up3[j], u3l[j], uh, uv);
+            }
         }
     }
 };
@@ -585,37 +666,42 @@ struct Chain<T, Q, Op, Rest...> {
 template <class T, int Q, int SCH, bool FWD>
 struct Pipe;
 
-// CDF 9/7 forward: pairs (alpha, beta), (gamma, delta).
+// CDF 9/7 forward: pairs (alpha, beta), (gamma, delta).  The forward runs the
+// scalar form of the float steps, the inverse the packed (float2) form: each
+// measured faster for its kernel (the forward kernel's register budget of 128
+// leaves no room for the register pairs).
 template <int Q>
 struct Pipe<float, Q, SCH_SEP, true> {
-    using type = Chain<float, Q, OpFTH<0, 1>, OpFTV<0, 1>, OpFSH<1, 1>, OpFSV<1, 1>, OpFTH<2, 1>,
-                       OpFTV<2, 1>, OpFSH<3, 1>, OpFSV<3, 1>>;
+    using type = Chain<float, Q, OpFTH<0, 1, false>, OpFTV<0, 1, false>, OpFSH<1, 1, false>,
+                       OpFSV<1, 1, false>, OpFTH<2, 1, false>, OpFTV<2, 1, false>,
+                       OpFSH<3, 1, false>, OpFSV<3, 1, false>>;
 };
 template <int Q>
 struct Pipe<float, Q, SCH_NONSEP, true> {
-    using type = Chain<float, Q, OpFT<0, 1, false>, OpFS<1, 1, false>, OpFT<2, 1, false>,
-                       OpFS<3, 1, false>>;
+    using type = Chain<float, Q, OpFT<0, 1, false, false>, OpFS<1, 1, false, false>,
+                       OpFT<2, 1, false, false>, OpFS<3, 1, false, false>>;
 };
 template <int Q>
 struct Pipe<float, Q, SCH_RED, true> {
-    using type =
-        Chain<float, Q, OpFT<0, 1, true>, OpFS<1, 1, true>, OpFT<2, 1, true>, OpFS<3, 1, true>>;
+    using type = Chain<float, Q, OpFT<0, 1, true, false>, OpFS<1, 1, true, false>,
+                       OpFT<2, 1, true, false>, OpFS<3, 1, true, false>>;
 };
 // CDF 9/7 inverse: undo every step in reverse order.
 template <int Q>
 struct Pipe<float, Q, SCH_SEP, false> {
-    using type = Chain<float, Q, OpFSV<3, -1>, OpFSH<3, -1>, OpFTV<2, -1>, OpFTH<2, -1>,
-                       OpFSV<1, -1>, OpFSH<1, -1>, OpFTV<0, -1>, OpFTH<0, -1>>;
+    using type = Chain<float, Q, OpFSV<3, -1, true>, OpFSH<3, -1, true>, OpFTV<2, -1, true>,
+                       OpFTH<2, -1, true>, OpFSV<1, -1, true>, OpFSH<1, -1, true>,
+                       OpFTV<0, -1, true>, OpFTH<0, -1, true>>;
 };
 template <int Q>
 struct Pipe<float, Q, SCH_NONSEP, false> {
-    using type = Chain<float, Q, OpFS<3, -1, false>, OpFT<2, -1, false>, OpFS<1, -1, false>,
-                       OpFT<0, -1, false>>;
+    using type = Chain<float, Q, OpFS<3, -1, false, true>, OpFT<2, -1, false, true>,
+                       OpFS<1, -1, false, true>, OpFT<0, -1, false, true>>;
 };
 template <int Q>
 struct Pipe<float, Q, SCH_RED, false> {
-    using type = Chain<float, Q, OpFS<3, -1, true>, OpFT<2, -1, true>, OpFS<1, -1, true>,
-                       OpFT<0, -1, true>>;
+    using type = Chain<float, Q, OpFS<3, -1, true, true>, OpFT<2, -1, true, true>,
+                       OpFS<1, -1, true, true>, OpFT<0, -1, true, true>>;
 };
 // LeGall 5/3 (reversible): the reduced scheme keeps the floors on whole 1-D
 // sums and is therefore the same integer dataflow as the non-separable one.

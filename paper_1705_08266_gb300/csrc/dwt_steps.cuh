@@ -15,6 +15,8 @@
 // (length 1) are passed as 0 (float) or the axis flag is false (integer).
 #pragma once
 
+#include <cuda_runtime.h>
+
 namespace dwt {
 
 // CDF 9/7 lifting constants (Daubechies & Sweldens factorisation, cited by the
@@ -26,83 +28,109 @@ constexpr float kDelta = 0.443506852043971f;
 constexpr float kK = 1.230174104914001f;
 
 // ---------------------------------------------------------------- float ----
+// Every float step is written once for V = float (one quadruple) and V =
+// float2 (two adjacent quadruples of a lane, one packed FP32 instruction per
+// pair).  Adds and multiplies are explicit round-to-nearest operations, so no
+// contraction differs between the two forms: both give the same bits.
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+template <class V>
+__device__ __forceinline__ V splat(float x);
+template <>
+__device__ __forceinline__ float splat<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float2 splat<float2>(float x) { return make_float2(x, x); }
+
 // Separable steps (Sec. 2 matrices T_P^H, T_P^V, S_U^H, S_U^V).
-__device__ __forceinline__ void f_TH(float& c1, float& c3, float c0, float c0r, float c2, float c2r,
-                                     float p) {
-    c1 = fmaf(p, c0 + c0r, c1);
-    c3 = fmaf(p, c2 + c2r, c3);
+template <class V>
+__device__ __forceinline__ void f_TH(V& c1, V& c3, V c0, V c0r, V c2, V c2r, float p) {
+    const V P = splat<V>(p);
+    c1 = vfma(P, vadd(c0, c0r), c1);
+    c3 = vfma(P, vadd(c2, c2r), c3);
 }
-__device__ __forceinline__ void f_TV(float& c2, float& c3, float c0, float n0, float c1, float n1,
-                                     float p) {
-    c2 = fmaf(p, c0 + n0, c2);
-    c3 = fmaf(p, c1 + n1, c3);
+template <class V>
+__device__ __forceinline__ void f_TV(V& c2, V& c3, V c0, V n0, V c1, V n1, float p) {
+    const V P = splat<V>(p);
+    c2 = vfma(P, vadd(c0, n0), c2);
+    c3 = vfma(P, vadd(c1, n1), c3);
 }
-__device__ __forceinline__ void f_SH(float& c0, float& c2, float c1, float c1l, float c3, float c3l,
-                                     float u) {
-    c0 = fmaf(u, c1 + c1l, c0);
-    c2 = fmaf(u, c3 + c3l, c2);
+template <class V>
+__device__ __forceinline__ void f_SH(V& c0, V& c2, V c1, V c1l, V c3, V c3l, float u) {
+    const V U = splat<V>(u);
+    c0 = vfma(U, vadd(c1, c1l), c0);
+    c2 = vfma(U, vadd(c3, c3l), c2);
 }
-__device__ __forceinline__ void f_SV(float& c0, float& c1, float c2, float up2, float c3, float up3,
-                                     float u) {
-    c0 = fmaf(u, c2 + up2, c0);
-    c1 = fmaf(u, c3 + up3, c1);
+template <class V>
+__device__ __forceinline__ void f_SV(V& c0, V& c1, V c2, V up2, V c3, V up3, float u) {
+    const V U = splat<V>(u);
+    c0 = vfma(U, vadd(c2, up2), c0);
+    c1 = vfma(U, vadd(c3, up3), c1);
 }
 
 // Spatial predict T_P (Sec. 3): rows [1,0,0,0], [P,1,0,0], [P*,0,1,0], [PP*,P*,P,1],
 // every term from pre-step values.  ph / pv: horizontal / vertical coefficient.
-__device__ __forceinline__ void f_T_plain(float& c1, float& c2, float& c3, float c0, float c0r,
-                                          float c2r, float n0, float n1, float n0r, float ph,
-                                          float pv) {
-    const float s00 = c0 + c0r;
-    const float s0d = c0 + n0;
-    const float q = (c2 + c2r) * ph + (c1 + n1) * pv;
-    const float n1new = fmaf(ph * pv, s00 + (n0 + n0r), q);
-    c1 = fmaf(ph, s00, c1);
-    c2 = fmaf(pv, s0d, c2);
-    c3 = c3 + n1new;
+template <class V>
+__device__ __forceinline__ void f_T_plain(V& c1, V& c2, V& c3, V c0, V c0r, V c2r, V n0, V n1,
+                                          V n0r, float ph, float pv) {
+    const V PH = splat<V>(ph), PV = splat<V>(pv), PHV = splat<V>(ph * pv);
+    const V s00 = vadd(c0, c0r);
+    const V s0d = vadd(c0, n0);
+    const V q = vfma(vadd(c2, c2r), PH, vmul(vadd(c1, n1), PV));
+    const V n1new = vfma(PHV, vadd(s00, vadd(n0, n0r)), q);
+    c1 = vfma(PH, s00, c1);
+    c2 = vfma(PV, s0d, c2);
+    c3 = vadd(c3, n1new);
 }
 
 // Spatial update S_U (Sec. 3): rows [1,U,U*,UU*], [0,1,0,U*], [0,0,1,U], [0,0,0,1].
-__device__ __forceinline__ void f_S_plain(float& c0, float& c1, float& c2, float c3, float c1l,
-                                          float c3l, float up2, float up3, float u3l, float uh,
-                                          float uv) {
-    const float t = (c1 + c1l) * uh + (c2 + up2) * uv;
-    const float d = fmaf(uh * uv, (c3 + c3l) + (up3 + u3l), t);
-    c1 = fmaf(uv, c3 + up3, c1);
-    c2 = fmaf(uh, c3 + c3l, c2);
-    c0 = c0 + d;
+template <class V>
+__device__ __forceinline__ void f_S_plain(V& c0, V& c1, V& c2, V c3, V c1l, V c3l, V up2, V up3,
+                                          V u3l, float uh, float uv) {
+    const V UH = splat<V>(uh), UV = splat<V>(uv), UHV = splat<V>(uh * uv);
+    const V t = vfma(vadd(c1, c1l), UH, vmul(vadd(c2, up2), UV));
+    const V d = vfma(UHV, vadd(vadd(c3, c3l), vadd(up3, u3l)), t);
+    c1 = vfma(UV, vadd(c3, up3), c1);
+    c2 = vfma(UH, vadd(c3, c3l), c2);
+    c0 = vadd(c0, d);
 }
 
 // Reduced spatial predict (Sec. 3, P = P0 + P1): the neighbour part P1 in the
 // non-separable matrix, then the constant part P0 in the separable scheme
 // (T^H(P0) then T^V(P0)); no barrier between the two.  9 MACs.
-__device__ __forceinline__ void f_T_red(float& c1, float& c2, float& c3, float c0, float c0r,
-                                        float c2r, float n0, float n1, float n0r, float ph,
-                                        float pv) {
-    c1 = fmaf(ph, c0r, c1);
-    c2 = fmaf(pv, n0, c2);
-    c3 = fmaf(ph, c2r, c3);
-    c3 = fmaf(pv, n1, c3);
-    c3 = fmaf(ph * pv, n0r, c3);
-    c1 = fmaf(ph, c0, c1);
-    c3 = fmaf(ph, c2, c3);
-    c2 = fmaf(pv, c0, c2);
-    c3 = fmaf(pv, c1, c3);
+template <class V>
+__device__ __forceinline__ void f_T_red(V& c1, V& c2, V& c3, V c0, V c0r, V c2r, V n0, V n1, V n0r,
+                                        float ph, float pv) {
+    const V PH = splat<V>(ph), PV = splat<V>(pv), PHV = splat<V>(ph * pv);
+    c1 = vfma(PH, c0r, c1);
+    c2 = vfma(PV, n0, c2);
+    c3 = vfma(PH, c2r, c3);
+    c3 = vfma(PV, n1, c3);
+    c3 = vfma(PHV, n0r, c3);
+    c1 = vfma(PH, c0, c1);
+    c3 = vfma(PH, c2, c3);
+    c2 = vfma(PV, c0, c2);
+    c3 = vfma(PV, c1, c3);
 }
 
 // Reduced spatial update: U1 part non-separably, then S^H(U0), S^V(U0).  9 MACs.
-__device__ __forceinline__ void f_S_red(float& c0, float& c1, float& c2, float c3, float c1l,
-                                        float c3l, float up2, float up3, float u3l, float uh,
-                                        float uv) {
-    c0 = fmaf(uh, c1l, c0);
-    c0 = fmaf(uv, up2, c0);
-    c0 = fmaf(uh * uv, u3l, c0);
-    c1 = fmaf(uv, up3, c1);
-    c2 = fmaf(uh, c3l, c2);
-    c0 = fmaf(uh, c1, c0);
-    c2 = fmaf(uh, c3, c2);
-    c0 = fmaf(uv, c2, c0);
-    c1 = fmaf(uv, c3, c1);
+template <class V>
+__device__ __forceinline__ void f_S_red(V& c0, V& c1, V& c2, V c3, V c1l, V c3l, V up2, V up3, V u3l,
+                                        float uh, float uv) {
+    const V UH = splat<V>(uh), UV = splat<V>(uv), UHV = splat<V>(uh * uv);
+    c0 = vfma(UH, c1l, c0);
+    c0 = vfma(UV, up2, c0);
+    c0 = vfma(UHV, u3l, c0);
+    c1 = vfma(UV, up3, c1);
+    c2 = vfma(UH, c3l, c2);
+    c0 = vfma(UH, c1, c0);
+    c2 = vfma(UH, c3, c2);
+    c0 = vfma(UV, c2, c0);
+    c1 = vfma(UV, c3, c1);
 }
 
 // -------------------------------------------------------------- integer ----
