@@ -40,6 +40,18 @@ struct StoreGeo {
     bool vec_hl, vec_lh;
 };
 
+// Row r's bands at `base` = mallat + r * pitch + g0; dlh = ne_r * pitch.
+template <class S, class T, int Q>
+__device__ __forceinline__ void store_details_at(const Quads<T, Q>& a, int r, const StoreGeo& g,
+                                                 S* base, long long dlh, bool lane_ok) {
+    if (!lane_ok || r < g.r_lo || r >= g.r_hi || r >= g.ne_r) return;
+    store_cols<S, T, Q>(base + g.ne_c, a.c[1], g.no_c - g.g0, g.vec_hl);
+    if (r < g.no_r) {
+        store_cols<S, T, Q>(base + dlh, a.c[2], g.ne_c - g.g0, g.vec_lh);
+        store_cols<S, T, Q>(base + dlh + g.ne_c, a.c[3], g.no_c - g.g0, g.vec_hl);
+    }
+}
+
 template <class S, class T, int Q>
 __device__ __forceinline__ void store_details(const Quads<T, Q>& a, int r, const StoreGeo& g,
                                               S* mallat, long long pitch, bool lane_ok) {
@@ -51,6 +63,14 @@ __device__ __forceinline__ void store_details(const Quads<T, Q>& a, int r, const
         store_cols<S, T, Q>(row2 + g.g0, a.c[2], g.ne_c - g.g0, g.vec_lh);
         store_cols<S, T, Q>(row2 + g.ne_c + g.g0, a.c[3], g.no_c - g.g0, g.vec_hl);
     }
+}
+
+// Row r's LL at `at` = ll + r * pitch + g0.
+template <class S, class T, int Q>
+__device__ __forceinline__ void store_ll_at(const Quads<T, Q>& a, int r, const StoreGeo& g, S* at,
+                                            bool lane_ok, bool vec) {
+    if (!lane_ok || r < g.r_lo || r >= g.r_hi || r >= g.ne_r) return;
+    store_cols<S, T, Q>(at, a.c[0], g.ne_c - g.g0, vec);
 }
 
 template <class S, class T, int Q>
@@ -133,10 +153,21 @@ struct FwdWarp {
         }
         e1.template push<EDGE, 4>(b1, q0, x1);
         const int r1 = q0 - LAG;  // first emitted level-1 row
+        {
+            // one row address per slot, advanced by the pitch (bands of row r
+            // at base, base + ne_c, base + ne_r pitch (+ ne_c))
+            S* base = mallat + (long long)r1 * mpitch + s1.g0;
+            const long long dlh = (long long)s1.ne_r * mpitch;
+            S* lrow = ll + (long long)r1 * llpitch + s1.g0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            store_details<S, T, Q1>(b1.r[k], r1 + k, s1, mallat, mpitch, lane_ok);
-            if constexpr (NL == 1) store_ll<S, T, Q1>(b1.r[k], r1 + k, s1, ll, llpitch, lane_ok, vec_ll);
+            for (int k = 0; k < 4; ++k) {
+                store_details_at<S, T, Q1>(b1.r[k], r1 + k, s1, base, dlh, lane_ok);
+                base += mpitch;
+                if constexpr (NL == 1) {
+                    store_ll_at<S, T, Q1>(b1.r[k], r1 + k, s1, lrow, lane_ok, vec_ll);
+                    lrow += llpitch;
+                }
+            }
         }
         if constexpr (NL >= 2) {
             // level-2 input rows q0/2 - 1 and q0/2 = LL rows q0 - 2 .. q0 + 1
@@ -152,10 +183,19 @@ struct FwdWarp {
             const int in2 = q0 / 2 - 1;
             e2.template push<EDGE, 2>(b2, in2, x2);
             const int r2 = in2 - LAG;
+            {
+                S* base = mallat + (long long)r2 * mpitch + s2.g0;
+                const long long dlh = (long long)s2.ne_r * mpitch;
+                S* lrow = ll + (long long)r2 * llpitch + s2.g0;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                store_details<S, T, Q2>(b2.r[k], r2 + k, s2, mallat, mpitch, lane_ok);
-                if constexpr (NL == 2) store_ll<S, T, Q2>(b2.r[k], r2 + k, s2, ll, llpitch, lane_ok, vec_ll);
+                for (int k = 0; k < 2; ++k) {
+                    store_details_at<S, T, Q2>(b2.r[k], r2 + k, s2, base, dlh, lane_ok);
+                    base += mpitch;
+                    if constexpr (NL == 2) {
+                        store_ll_at<S, T, Q2>(b2.r[k], r2 + k, s2, lrow, lane_ok, vec_ll);
+                        lrow += llpitch;
+                    }
+                }
             }
             if constexpr (NL >= 3) {
                 static_assert(Q1 >= 4, "three fused levels need 4 columns per lane");

@@ -58,7 +58,9 @@ struct InvWarpT {
     S* out;
     long long opitch;
     int out_h, out_w, xb, lane, A0, A1;
+    int x0l;        // first output column of this lane
     bool lane_ok, vec_out;
+    bool vec_row;   // this lane's 2 Q1 output columns are one aligned vector inside the row
 
     template <bool EDGE>
     __device__ __forceinline__ void slot(const S* sm, int q0, bool level1) {
@@ -104,38 +106,40 @@ struct InvWarpT {
         }
         e1.template push<EDGE, 4>(b1, q0, x1);
         const int r1 = q0 - LAG;
+        // quadruple row r -> output rows 2r (c0 c1 interleaved) and 2r + 1
+        // (c2 c3); one row address per slot, advanced by the pitch
+        S* p = out + (long long)(2 * r1) * opitch + x0l;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) store_quad_row(b1.r[k], r1 + k);
-    }
-
-    // Quadruple row r -> output rows 2r (c0 c1 interleaved) and 2r + 1 (c2 c3).
-    __device__ __forceinline__ void store_quad_row(const Quads<T, Q1>& a, int r) {
-        if (!lane_ok || r < A0 || r >= A1) return;
-        T ev[2 * Q1], od[2 * Q1];
+        for (int k = 0; k < 4; ++k) {
+            const int r = r1 + k;
+            if (lane_ok && r >= A0 && r < A1) {
+                T ev[2 * Q1], od[2 * Q1];
 #pragma unroll
-        for (int j = 0; j < Q1; ++j) {
-            ev[2 * j] = a.c[0][j];
-            ev[2 * j + 1] = a.c[1][j];
-            od[2 * j] = a.c[2][j];
-            od[2 * j + 1] = a.c[3][j];
+                for (int j = 0; j < Q1; ++j) {
+                    ev[2 * j] = b1.r[k].c[0][j];
+                    ev[2 * j + 1] = b1.r[k].c[1][j];
+                    od[2 * j] = b1.r[k].c[2][j];
+                    od[2 * j + 1] = b1.r[k].c[3][j];
+                }
+                store_px(ev, 2 * r, p);
+                store_px(od, 2 * r + 1, p + opitch);
+            }
+            p += 2 * opitch;
         }
-        store_px(ev, 2 * r);
-        store_px(od, 2 * r + 1);
     }
 
-    __device__ __forceinline__ void store_px(const T (&v)[2 * Q1], int y) {
+    // Output row y at p (= out + y * opitch + x0l).
+    __device__ __forceinline__ void store_px(const T (&v)[2 * Q1], int y, S* p) {
         if (y >= out_h) return;
-        const int x0 = xb + 2 * Q1 * lane;
-        S* p = out + (long long)y * opitch + x0;
         S w[2 * Q1];
 #pragma unroll
         for (int j = 0; j < 2 * Q1; ++j) w[j] = Storage<S>::st(v[j]);
-        if (vec_out && x0 + 2 * Q1 <= out_w) {
+        if (vec_row) {
             st_vec<S, 2 * Q1>(p, w);
         } else {
 #pragma unroll
             for (int j = 0; j < 2 * Q1; ++j)
-                if (x0 + j >= 0 && x0 + j < out_w) p[j] = w[j];
+                if (x0l + j >= 0 && x0l + j < out_w) p[j] = w[j];
         }
     }
 };
@@ -180,6 +184,8 @@ __device__ __forceinline__ void inv_body(const CUtensorMap* m1p, const CUtensorM
     w.out_h = a.lv[0].h;
     w.out_w = a.lv[0].w;
     w.vec_out = (a.out_pitch % (2 * Q1)) == 0;
+    w.x0l = w.xb + 2 * Q1 * lane;
+    w.vec_row = w.vec_out && w.x0l >= 0 && w.x0l + 2 * Q1 <= a.lv[0].w;
     const int ne1 = (a.lv[0].h + 1) >> 1;
     w.A0 = seg * a.segq;
     w.A1 = min(w.A0 + a.segq, ne1);
