@@ -39,6 +39,7 @@ struct dwt2d_plan_s {
     // at fwd_warps_large warps runs that many (several waves even out the
     // strips' unequal costs); smaller launches keep fwd_warps_target
     int fwd_warps_large, large_segq;
+    int inv_warps_large;  // the same rule for inverse launches
     int fwd_q1;  // quadruple columns per lane of the forward kernel (2 or 4)
     int inv_q1;  // the same for the inverse
     int min_segq;
@@ -343,6 +344,16 @@ dwt2d_status build_group(const dwt2d_plan_s* p, bool fwd, int k, const void* src
         if (s != DWT2D_OK) return s;
         decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, q1, inv_target, &a, &out->grid,
                   kInvTmaWarps, segq_fixed);
+        if (segq_fixed <= 0 && p->inv_warps_large > inv_target) {
+            FusedArgs b = a;
+            int grid_b = 0;
+            decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, q1, p->inv_warps_large, &b, &grid_b,
+                      kInvTmaWarps);
+            if (b.segq >= p->large_segq) {
+                a = b;
+                out->grid = grid_b;
+            }
+        }
         out->path = 1;
         out->q1 = q1;
     } else {
@@ -612,11 +623,15 @@ static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width
                                                                     : env_int("DWT2D_INV_WARPS_PER_SM", 12));
     p->min_segq = tuning && tuning->min_segment > 0 ? tuning->min_segment : env_int("DWT2D_MIN_SEGQ", 2);
     // measured at 8192^2: the first forward launch is fastest at about 44
-    // warps per SM (2.75 waves), the small later ones at one wave
+    // warps per SM (2.75 waves of 16), the small later ones at one wave
     p->fwd_warps_large = tuning && tuning->warps_per_sm > 0
                              ? 0
                              : sms * env_int("DWT2D_FWD_WARPS_PER_SM_LARGE", 44);
     p->large_segq = env_int("DWT2D_LARGE_SEGQ", 16);
+    // the finest inverse launch: about 24 warps per SM (2 waves of 12)
+    p->inv_warps_large = tuning && tuning->warps_per_sm > 0
+                             ? 0
+                             : sms * env_int("DWT2D_INV_WARPS_PER_SM_LARGE", 24);
     p->fwd_q1 = env_int("DWT2D_FWD_Q", 2) == 4 && !half ? 4 : 2;
     p->inv_q1 = env_int("DWT2D_INV_Q", 2) == 4 && !half ? 4 : 2;
 
