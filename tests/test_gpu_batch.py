@@ -199,3 +199,25 @@ def test_single_item_batch_and_round_trip():
     assert torch.equal(mid.cpu(), ref.cpu())
     maxabs = float(np.max(np.abs(x)))
     assert float(np.max(np.abs(out.cpu().numpy() - x))) <= 2 * 5 * TOL_F32 * maxabs
+
+
+def test_autotune_picks_a_candidate_and_caches(tmp_path):
+    from paper_1705_08266_gb300 import autotune
+
+    jobs, _ = _jobs(MIXED[:6], 77)
+    cands = [{"fuse_first": 2, "fuse_max": 2, "warps_per_sm": w, "min_segment": 2} for w in (12, 48)]
+    cands.append({"fuse_first": 2, "fuse_max": 3, "warps_per_sm": 16, "min_segment": 2})  # refused
+    path = str(tmp_path / "tune.json")
+    best = autotune.tune(jobs, cache_path=path, iters=2, warmup=1, candidates=cands)
+    assert best in cands[:2]
+    import json
+    entry = next(iter(json.load(open(path)).values()))
+    assert len(entry["tried"]) == 2 and entry["tuning"] == best
+    # the tuned batch computes the same coefficients as the single-image calls
+    b = D.Batch(jobs, tuning=best)
+    ws = b.workspace()
+    b.upload(ws)
+    b.launch(ws)
+    torch.cuda.synchronize()
+    assert b.status(ws) == 0
+    _assert_same_as_single(jobs, "nonsep_reduced", "autotuned")
