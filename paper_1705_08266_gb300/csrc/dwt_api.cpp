@@ -909,7 +909,8 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
                         delete b;
                         return DWT2D_ERR_INVALID;
                     }
-                    L.grid = (int)((warps + 3) / 4);
+                    const int per_cta = fwd ? kFwdWarps : kInvTmaWarps;
+                    L.grid = (int)((warps + per_cta - 1) / per_cta);
                     b->warps += warps;
                     b->launches.push_back(L);
                 }

@@ -231,7 +231,9 @@ __device__ __forceinline__ bool rows_interior(int q0, int nl, int lag, const int
 }
 
 template <int Q1>
-__host__ __device__ constexpr int fwd_min_blocks() { return Q1 <= 2 ? 4 : 2; }
+// CTAs per SM the register budget is sized for: 16 warps (128 registers) with
+// 2 quadruple columns per lane, 8 warps with 4.
+__host__ __device__ constexpr int fwd_min_blocks() { return (Q1 <= 2 ? 16 : 8) / kFwdWarps; }
 
 // One warp's work item `wid` of a launch described by `a` (input through the
 // tensor map at `mapp`).
@@ -368,9 +370,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
 // Many images in one launch: warp w of the grid works on entry i with
 // first[i] <= w < first[i + 1] of a table in device memory.  The arguments
 // come from registers instead of the constant bank, so the kernel gets the
-// register budget of 3 CTAs per SM (no spills) rather than 4.
+// register budget of 12 warps per SM (no spills) rather than 16.
 template <class S, int SCH, int NL, int Q1>
-__global__ void __launch_bounds__(kFwdWarps * 32, 3)
+__global__ void __launch_bounds__(kFwdWarps * 32, 12 / kFwdWarps)
     fwd_batched_kernel(const BatchEntry* __restrict__ table, int n) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int gw = blockIdx.x * kFwdWarps + (threadIdx.x >> 5);
