@@ -98,7 +98,7 @@ cudaError_t launch_inv_tma(int elem, int scheme, int nl, int q1, const CUtensorM
                            const CUtensorMap& m2, const CUtensorMap& ml, const FusedArgs& a,
                            int grid, cudaStream_t st);
 size_t inv_tma_smem_bytes(int elem_bytes, int nl, int q1);
-constexpr int kInvTmaWarps = 4;
+constexpr int kInvTmaWarps = 1;  // one-warp CTAs, as the forward
 
 // One level of the separable convolution scheme (Sec. 2, Eq. 1).
 struct ConvArgs {

@@ -17,7 +17,7 @@
 
 namespace dwt {
 
-constexpr int kInvWarps = 4;  // warps per CTA (independent)
+constexpr int kInvWarps = kInvTmaWarps;  // warps per CTA (independent)
 constexpr int kInvSlots = 3;  // ring depth per warp
 
 // Box widths carry A extra elements (16 bytes) so a box can start at the
@@ -288,8 +288,9 @@ __device__ __forceinline__ void inv_body(const CUtensorMap* m1p, const CUtensorM
     }
 }
 
+// 12 warps per SM (168 registers) with 2 quadruple columns per lane, 8 with 4
 template <class S, int SCH, int NL, int Q1>
-__global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
+__global__ void __launch_bounds__(kInvWarps * 32, (Q1 <= 2 ? 12 : 8) / kInvWarps)
     inv_tma_kernel(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2,
                    const __grid_constant__ CUtensorMap ml, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
 }
 
 template <class S, int SCH, int NL, int Q1>
-__global__ void __launch_bounds__(kInvWarps * 32, Q1 <= 2 ? 3 : 2)
+__global__ void __launch_bounds__(kInvWarps * 32, (Q1 <= 2 ? 12 : 8) / kInvWarps)
     inv_batched_kernel(const BatchEntry* __restrict__ table, int n) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int gw = blockIdx.x * kInvWarps + (threadIdx.x >> 5);
