@@ -56,7 +56,12 @@ def parse():
     return ap.parse_args()
 
 
+_REDUCE_DEVICE = "cuda"
+
+
 def dist_setup():
+    """One process per GPU (torchrun env); NCCL on GPUs, gloo without (host tests)."""
+    global _REDUCE_DEVICE
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -64,8 +69,13 @@ def dist_setup():
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         import torch.distributed as dist
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            _REDUCE_DEVICE = "cuda"
+        else:
+            dist.init_process_group("gloo")
+            _REDUCE_DEVICE = "cpu"
     return ws, rank, local
 
 
@@ -81,7 +91,7 @@ def max_over_ranks(ws, v: float) -> float:
         return v
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=_REDUCE_DEVICE)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
