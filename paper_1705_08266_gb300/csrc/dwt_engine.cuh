@@ -223,6 +223,25 @@ __device__ __forceinline__ void unpk(float2 p, float (&v)[Q], int j) {
     v[j + 1] = p.y;
 }
 
+// Row segment of the k-th segment slot when segments are taken in F
+// interleaved groups ({0, F, 2F, ..}, then {1, F + 1, ..}, ..): with F waves
+// of warps, a segment starts about when the one above it ends, so the halo
+// rows they share are still in L2.
+__device__ __forceinline__ int seg_order(int k, int nsegs, int f) {
+    if (f <= 1 || nsegs <= 1) return k;
+    const int q = nsegs / f, r = nsegs % f;
+    int i, j;
+    if (k < r * (q + 1)) {
+        i = k / (q + 1);
+        j = k % (q + 1);
+    } else {
+        const int kk = k - r * (q + 1);
+        i = r + kk / q;
+        j = kk % q;
+    }
+    return j * f + i;
+}
+
 enum Kind { K_NONE = 0, K_DOWN = 1, K_UP = 2 };
 
 // ------------------------------------------------------------------ ops ----

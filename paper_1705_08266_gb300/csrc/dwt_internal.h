@@ -33,6 +33,7 @@ struct FusedArgs {
     void* out;
     long long out_pitch;
     int nstrips, nsegs, segq;        // warp work items = nstrips * nsegs
+    int seg_f;                       // segment order interleave (<= 1: top to bottom)
     int valid_px, xoff;              // strip width in input pixels and left halo offset
     int lane_lo, lane_hi;            // lanes that store
     int* err;                        // device status word (0 = ok)
