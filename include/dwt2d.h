@@ -142,7 +142,13 @@ dwt2d_status dwt2d_inverse(dwt2d_plan_t plan, const void* d_src, int64_t src_pit
  * dwt2d_forward_host / dwt2d_inverse_host -- the same transform on HOST
  *   buffers: copies h_src (host, pitch h_src_pitch_bytes; pinned memory for
  *   overlap) into d_stage_in, transforms into d_stage_out, copies d_stage_out
- *   back to h_dst, all on stream, then synchronizes stream.
+ *   back to h_dst, then synchronizes stream.  The forward of a fused-lifting
+ *   plan with at least 1024 rows overlaps the three: the image goes in by row
+ *   bands on an internal stream, the first level group runs on `stream` band
+ *   by band as its input rows arrive, and the finished detail bands come back
+ *   on a second internal stream while later bands still go in (the plan owns
+ *   the two streams; a plan's _host calls must not overlap each other).  The
+ *   inverse runs copy, transform, copy on `stream`.
  *   d_stage_in, d_stage_out: device buffers of height rows x d_pitch_bytes.
  *   Errors: as dwt2d_forward, plus DWT2D_ERR_CUDA for a failed copy.
  */

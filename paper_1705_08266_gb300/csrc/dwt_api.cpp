@@ -50,6 +50,10 @@ struct dwt2d_plan_s {
     // profiling hook: events[2i] / events[2i+1] around launch i
     cudaEvent_t* events;
     int nevents;
+    // host-buffer forward: copy streams and events (created on first use)
+    bool host_ready;
+    cudaStream_t host_in, host_out;
+    cudaEvent_t host_ev[2 * 8 + 3];
 };
 
 // A batch: per-image plans, workspace regions and the launch list.
@@ -730,6 +734,142 @@ dwt2d_status dwt2d_inverse(dwt2d_plan_t p, const void* d_src, int64_t sp, void* 
                                 : run_fused(p, false, d_src, sp, d_dst, dp, d_ws, as_stream(stream));
 }
 
+constexpr int kHostBands = 8;
+
+static bool host_resources(dwt2d_plan_s* p) {
+    if (p->host_ready) return true;
+    if (cudaStreamCreateWithFlags(&p->host_in, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaStreamCreateWithFlags(&p->host_out, cudaStreamNonBlocking) != cudaSuccess) return false;
+    for (auto& e : p->host_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+    p->host_ready = true;
+    return true;
+}
+
+// Rows of the first group's input that row segment s reads (its TMA boxes),
+// as the forward kernel computes them: [0, end).
+static int seg_input_end(const dwt2d_plan_s* p, const FusedArgs& a, int nl, int rho, int s) {
+    const int neN = (a.lv[nl - 1].h + 1) >> 1;
+    const int R0 = s * a.segq, R1 = std::min(R0 + a.segq, neN);
+    int f = R0, e = R1 - 1;
+    for (int l = nl; l >= 1; --l) {
+        f -= rho;
+        e += rho;
+        if (l > 1) {
+            f *= 2;
+            e = 2 * e + 1;
+        }
+    }
+    const int qstart = std::max(f, 0) & ~3, qend = e + 1;
+    const int nslots = (qend - qstart + 3) / 4;
+    return std::min(2 * qstart + kFwdSlotRows * nslots, p->H);
+}
+
+// Host image -> host coefficients with the copies overlapped with the
+// transform.  The image goes in as row bands on one stream; the first level
+// group runs as one launch per run of row segments whose input rows have
+// arrived; the detail bands those segments finish go out on a second stream
+// while later bands still come in; the top-left region the later groups
+// write goes out last.  The link carries about 200 GB/s each way and about
+// 330 GB/s both ways at once, so overlapping the two directions is the gain.
+static dwt2d_status run_host_fwd_pipelined(dwt2d_plan_s* p, const void* h_src, int64_t hsp,
+                                           void* h_dst, int64_t hdp, void* d_in, void* d_out,
+                                           int64_t dpitch, void* d_ws, cudaStream_t st) {
+    const int64_t es = p->elem;
+    const int64_t row = (int64_t)p->W * es;
+    const char* hs = reinterpret_cast<const char*>(h_src);
+    char* hd = reinterpret_cast<char*>(h_dst);
+    char* din = reinterpret_cast<char*>(d_in);
+    char* dout = reinterpret_cast<char*>(d_out);
+    char* wsb = reinterpret_cast<char*>(d_ws);
+    int* err = reinterpret_cast<int*>(wsb);
+    cudaEvent_t* ev = p->host_ev;  // [0] start, [1..8] bands in, [9..16] launches, [17] end, [18] out
+    auto copy2d = [](char* dst, int64_t dp, const char* src, int64_t sp, int64_t w, int64_t rows,
+                     cudaMemcpyKind kind, cudaStream_t s) {
+        if (rows <= 0 || w <= 0) return cudaSuccess;
+        if (dp == w && sp == w) return cudaMemcpyAsync(dst, src, (size_t)(w * rows), kind, s);
+        return cudaMemcpy2DAsync(dst, dp, src, sp, w, rows, kind, s);
+    };
+    // begin after the caller's earlier work on st (it may still use the buffers)
+    if (cudaEventRecord(ev[0], st) != cudaSuccess || cudaStreamWaitEvent(p->host_in, ev[0], 0) ||
+        cudaStreamWaitEvent(p->host_out, ev[0], 0))
+        return DWT2D_ERR_CUDA;
+    const int rb = (p->H + kHostBands - 1) / kHostBands;
+    for (int c = 0; c < kHostBands; ++c) {
+        const int r0 = std::min(c * rb, p->H), r1 = std::min(r0 + rb, p->H);
+        if (copy2d(din + r0 * dpitch, dpitch, hs + r0 * hsp, hsp, row, r1 - r0, cudaMemcpyHostToDevice,
+                   p->host_in) != cudaSuccess ||
+            cudaEventRecord(ev[1 + c], p->host_in) != cudaSuccess)
+            return DWT2D_ERR_CUDA;
+    }
+    const int elem_kind = elem_kind_of(p->dtype);
+    const int sch = base_scheme(p->scheme);
+    const int rho = p->wavelet == DWT2D_CDF97 ? 2 : 1;
+    GroupLaunch g0;
+    dwt2d_status s = build_group(p, true, 0, d_in, dpitch / es, d_out, dpitch / es, wsb, err,
+                                 p->fwd_warps_target, p->inv_warps_target, &g0);
+    if (s != DWT2D_OK) return s;
+    const int nl0 = g0.nl;
+    FusedArgs base = g0.a;
+    base.seg_f = 1;
+    int next = 0;  // first segment not launched yet
+    for (int c = 0; c < kHostBands && next < base.nsegs; ++c) {
+        const int avail = std::min((c + 1) * rb, p->H);
+        int end = next;
+        while (end < base.nsegs && (c == kHostBands - 1 || seg_input_end(p, base, nl0, rho, end) <= avail))
+            ++end;
+        if (end == next) continue;
+        FusedArgs a = base;
+        a.seg_lo = next;
+        a.nsegs = end - next;
+        const int grid = (a.nstrips * a.nsegs + kFwdWarps - 1) / kFwdWarps;
+        if (cudaStreamWaitEvent(st, ev[1 + c], 0) != cudaSuccess ||
+            launch_fwd_fused(elem_kind, sch, nl0, g0.q1, g0.m[0], a, grid, st) != cudaSuccess ||
+            cudaEventRecord(ev[9 + c], st) != cudaSuccess ||
+            cudaStreamWaitEvent(p->host_out, ev[9 + c], 0) != cudaSuccess)
+            return DWT2D_ERR_CUDA;
+        // the detail bands of levels 1..nl0 in these segments' rows are final
+        for (int l = 0; l < nl0; ++l) {
+            const int h = a.lv[l].h, w = a.lv[l].w;
+            const int ne_r = (h + 1) >> 1, no_r = h >> 1, ne_c = (w + 1) >> 1;
+            const int sh = nl0 - 1 - l;
+            const int neN = (a.lv[nl0 - 1].h + 1) >> 1;
+            const int q0 = (next * a.segq) << sh;
+            const int q1 = std::min(std::min(end * a.segq, neN) << sh, ne_r);
+            if (q1 <= q0) continue;
+            // HL: rows [q0, q1), columns [ne_c, w)
+            if (copy2d(hd + q0 * hdp + ne_c * es, hdp, dout + q0 * dpitch + ne_c * es, dpitch,
+                       (int64_t)(w - ne_c) * es, q1 - q0, cudaMemcpyDeviceToHost, p->host_out) != cudaSuccess)
+                return DWT2D_ERR_CUDA;
+            // LH and HH: rows [ne_r + q0, ne_r + min(q1, no_r)), columns [0, w)
+            const int r1 = std::min(q1, no_r);
+            if (r1 > q0 && copy2d(hd + (ne_r + q0) * hdp, hdp, dout + (ne_r + q0) * dpitch, dpitch,
+                                  (int64_t)w * es, r1 - q0, cudaMemcpyDeviceToHost, p->host_out) != cudaSuccess)
+                return DWT2D_ERR_CUDA;
+        }
+        next = end;
+    }
+    // every band has arrived before the call returns (the input buffer is free)
+    if (cudaStreamWaitEvent(st, ev[kHostBands], 0) != cudaSuccess) return DWT2D_ERR_CUDA;
+    for (int k = 1; k < p->ngroups; ++k) {
+        GroupLaunch gl;
+        s = build_group(p, true, k, d_in, dpitch / es, d_out, dpitch / es, wsb, err, p->fwd_warps_target,
+                        p->inv_warps_target, &gl);
+        if (s != DWT2D_OK) return s;
+        if (launch_fwd_fused(elem_kind, sch, gl.nl, gl.q1, gl.m[0], gl.a, gl.grid, st) != cudaSuccess)
+            return DWT2D_ERR_CUDA;
+    }
+    // the region of the later levels (and the last LL): rows [0, ne_r), columns [0, ne_c)
+    const int hl = base.lv[nl0 - 1].h, wl = base.lv[nl0 - 1].w;
+    const int ner = (hl + 1) >> 1, nec = (wl + 1) >> 1;
+    if (cudaEventRecord(ev[17], st) != cudaSuccess || cudaStreamWaitEvent(p->host_out, ev[17], 0) ||
+        copy2d(hd, hdp, dout, dpitch, (int64_t)nec * es, ner, cudaMemcpyDeviceToHost, p->host_out) !=
+            cudaSuccess ||
+        cudaEventRecord(ev[18], p->host_out) != cudaSuccess || cudaStreamWaitEvent(st, ev[18], 0))
+        return DWT2D_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? DWT2D_OK : DWT2D_ERR_CUDA;
+}
+
 static dwt2d_status run_host(dwt2d_plan_t p, bool fwd, const void* h_src, int64_t hsp, void* h_dst,
                              int64_t hdp, void* d_in, void* d_out, int64_t dpitch, void* d_ws,
                              float scale, void* stream) {
@@ -737,13 +877,22 @@ static dwt2d_status run_host(dwt2d_plan_t p, bool fwd, const void* h_src, int64_
     const int64_t row = (int64_t)p->W * p->elem;
     if (hsp < row || hdp < row) return DWT2D_ERR_INVALID;
     cudaStream_t st = as_stream(stream);
-    if (cudaMemcpy2DAsync(d_in, dpitch, h_src, hsp, row, p->H, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return DWT2D_ERR_CUDA;
+    if (fwd && p->H >= 1024 && !multipass(p->scheme) && !convolution(p->scheme) &&
+        env_int("DWT2D_HOST_PIPELINE", 1) != 0 && check_buffers(p, d_in, dpitch, d_out, dpitch, d_ws) ==
+                                                      DWT2D_OK &&
+        p->groups[0].n <= 2 && scale_ok(p, scale) && host_resources(p))
+        return run_host_fwd_pipelined(p, h_src, hsp, h_dst, hdp, d_in, d_out, dpitch, d_ws, st);
+    // one linear copy when both sides are unpadded (faster than a 2-D copy)
+    auto copy = [&](void* dst, int64_t dp, const void* src, int64_t sp, cudaMemcpyKind kind) {
+        if (dp == row && sp == row)
+            return cudaMemcpyAsync(dst, src, (size_t)row * p->H, kind, st);
+        return cudaMemcpy2DAsync(dst, dp, src, sp, row, p->H, kind, st);
+    };
+    if (copy(d_in, dpitch, h_src, hsp, cudaMemcpyHostToDevice) != cudaSuccess) return DWT2D_ERR_CUDA;
     dwt2d_status s = fwd ? dwt2d_forward(p, d_in, dpitch, d_out, dpitch, d_ws, scale, stream)
                          : dwt2d_inverse(p, d_in, dpitch, d_out, dpitch, d_ws, scale, stream);
     if (s != DWT2D_OK) return s;
-    if (cudaMemcpy2DAsync(h_dst, hdp, d_out, dpitch, row, p->H, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        return DWT2D_ERR_CUDA;
+    if (copy(h_dst, hdp, d_out, dpitch, cudaMemcpyDeviceToHost) != cudaSuccess) return DWT2D_ERR_CUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? DWT2D_OK : DWT2D_ERR_CUDA;
 }
 
@@ -813,7 +962,14 @@ dwt2d_status dwt2d_plan_set_launch_events(dwt2d_plan_t p, void** events, int32_t
     return DWT2D_OK;
 }
 
-void dwt2d_plan_destroy(dwt2d_plan_t p) { free(p); }
+void dwt2d_plan_destroy(dwt2d_plan_t p) {
+    if (p && p->host_ready) {
+        cudaStreamDestroy(p->host_in);
+        cudaStreamDestroy(p->host_out);
+        for (auto& e : p->host_ev) cudaEventDestroy(e);
+    }
+    free(p);
+}
 
 dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* items, int32_t n,
                                 dwt2d_scheme scheme, const dwt2d_tuning* tuning,

@@ -256,7 +256,7 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArg
                      warp * kFwdSlots;
 
     const int strip = wid % a.nstrips;
-    const int seg = seg_order(wid / a.nstrips, a.nsegs, a.seg_f);
+    const int seg = a.seg_lo + seg_order(wid / a.nstrips, a.nsegs, a.seg_f);
     const int xb = strip * a.valid_px - a.xoff;
 
     // rows of the last fused level this item produces, and the input rows it needs

@@ -34,6 +34,7 @@ struct FusedArgs {
     long long out_pitch;
     int nstrips, nsegs, segq;        // warp work items = nstrips * nsegs
     int seg_f;                       // segment order interleave (<= 1: top to bottom)
+    int seg_lo;                      // first row segment of this launch (launches over a subset)
     int valid_px, xoff;              // strip width in input pixels and left halo offset
     int lane_lo, lane_hi;            // lanes that store
     int* err;                        // device status word (0 = ok)

@@ -174,7 +174,7 @@ __device__ __forceinline__ void inv_body(const CUtensorMap* m1p, const CUtensorM
                      warp * kInvSlots;
 
     const int strip = wid % a.nstrips;
-    const int seg = seg_order(wid / a.nstrips, a.nsegs, a.seg_f);
+    const int seg = a.seg_lo + seg_order(wid / a.nstrips, a.nsegs, a.seg_f);
     W w;
     w.lane = lane;
     w.xb = strip * a.valid_px - a.xoff;

@@ -137,3 +137,33 @@ def test_host_entry_points():
     back = torch.empty_like(hs).pin_memory()
     plan.inverse_host(hd, back, din, dout, ws)
     assert np.max(np.abs(back.numpy() - x)) <= 1e-5 * np.max(np.abs(x))
+
+
+@pytest.mark.parametrize("h,w,levels,wavelet,dtype", [
+    (1030, 2050, 5, "cdf97", torch.float32), (2048, 1536, 3, "legall53", torch.int32),
+    (4097, 333, 2, "cdf97", torch.float32), (1024, 1024, 1, "cdf97", torch.float32),
+    (1500, 900, 6, "cdf97", torch.float16), (3001, 777, 4, "legall53", torch.int32)])
+def test_host_forward_pipelined_equals_device_forward(h, w, levels, wavelet, dtype):
+    """The host-buffer forward overlaps its copies with the transform by row
+    bands; the coefficients are the device entry point's, bit for bit."""
+    x = make_input(wavelet, h, w, seed=h + w)
+    if dtype == torch.float16:
+        x = x / float(np.max(np.abs(x)))
+    xt = torch.from_numpy(x).to(dtype)
+    plan = D.Plan(h, w, levels, wavelet, "nonsep_reduced", dtype)
+    ws = plan.workspace()
+    hs = xt.pin_memory()
+    hd = torch.full_like(hs, 7).pin_memory()
+    din = D.empty_image(h, w, dtype)
+    dout = D.empty_image(h, w, dtype)
+    plan.forward_host(hs, hd, din, dout, ws)
+    ref = plan.forward(device_image(x).to(dtype) if dtype != torch.float16 else _dev16(xt))
+    torch.cuda.synchronize()
+    assert torch.equal(hd, ref.cpu())
+    assert plan.status(ws) == 0
+
+
+def _dev16(t):
+    d = D.empty_image(t.shape[0], t.shape[1], t.dtype)
+    d.copy_(t)
+    return d
