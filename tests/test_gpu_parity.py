@@ -13,8 +13,8 @@ import torch
 
 from oracle import lifting as L
 from paper_1705_08266_gb300 import dwt2d as D
-from tests.parity_util import (assert_forward_matches, assert_inverse_matches, device_image, host,
-                               make_input)
+from tests.parity_util import (TOL_F32, assert_forward_matches, assert_inverse_matches, device_image,
+                               host, make_input)
 
 pytestmark = pytest.mark.gpu
 
@@ -167,3 +167,27 @@ def _dev16(t):
     d = D.empty_image(t.shape[0], t.shape[1], t.dtype)
     d.copy_(t)
     return d
+
+
+@pytest.mark.parametrize("wavelet", ["cdf97", "legall53"])
+@pytest.mark.parametrize("shape,levels", [((130, 257), 5), ((1030, 2050), 5), ((777, 3001), 2)])
+def test_cross_scheme_agreement(wavelet, shape, levels):
+    """Separable, non-separable and reduced lifting compute one transform:
+    bit-exact for the integer 5/3 (nested floors reproduce the separable
+    order); for FP32 9/7 within twice the per-scheme oracle tolerance (each is
+    within TOL_F32 * max|x| of the FP64 result)."""
+    h, w = shape
+    x = make_input(wavelet, h, w, seed=h * 7 + w)
+    xd = device_image(x)
+    outs = {}
+    for scheme in ("separable", "nonsep", "nonsep_reduced", "nonsep_multipass"):
+        outs[scheme] = D.Plan(h, w, levels, wavelet, scheme).forward(xd).cpu()
+    torch.cuda.synchronize()
+    ref = outs["separable"]
+    for scheme, got in outs.items():
+        if wavelet == "legall53":
+            assert torch.equal(got, ref), scheme
+        else:
+            maxabs = float(np.max(np.abs(x)))
+            d = float((got.double() - ref.double()).abs().max())
+            assert d <= 2 * TOL_F32 * maxabs, (scheme, d / maxabs)
