@@ -88,7 +88,9 @@ typedef enum {
     DWT2D_ERR_ALIGN = -3,       /* pointer or pitch alignment */
     DWT2D_ERR_NOMEM = -4,       /* host allocation of the plan failed */
     DWT2D_ERR_CUDA = -5,        /* a CUDA call or launch failed */
-    DWT2D_ERR_TIMEOUT = -6      /* a kernel gave up a bounded wait */
+    DWT2D_ERR_TIMEOUT = -6,     /* a kernel gave up a bounded wait */
+    DWT2D_ERR_BOUNDS = -7       /* a bounds-checked build (DWT_BOUNDS_CHECK) caught a store
+                                   outside its buffer (the store was skipped) */
 } dwt2d_status;
 
 /*

@@ -18,6 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdwt2d.so")
+BUILD_BOUNDS = os.path.join(HERE, "_build_bounds")
+LIB_BOUNDS = os.path.join(HERE, "libdwt2d_bounds.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -39,9 +41,9 @@ def cuda_include() -> str:
     return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "include")
 
 
-def _compile(src: str, extra) -> str:
+def _compile(src: str, extra, build_dir: str = BUILD) -> str:
     stem, ext = os.path.splitext(os.path.basename(src))
-    obj = os.path.join(BUILD, stem + ".o")
+    obj = os.path.join(build_dir, stem + ".o")
     if ext == ".cpp":
         cxx = os.environ.get("CXX") or shutil.which("g++") or "g++"
         cmd = [cxx, "-O2", "-std=c++20", "-fPIC", "-Wall", "-I", cuda_include(), "-I", INCLUDE,
@@ -54,10 +56,10 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def _stale(objs) -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     deps.append(os.path.join(INCLUDE, "dwt2d.h"))
     deps.append(os.path.abspath(__file__))
@@ -66,22 +68,32 @@ def _stale(objs) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     """Compile every kernel file and link libdwt2d.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and not _stale(None):
-        return LIB
+    return _build(LIB, BUILD, force, verbose, extra)
+
+
+def build_bounds_checked(force: bool = False) -> str:
+    """The same library with every streaming-kernel store checked against its
+    buffer (DWT_BOUNDS_CHECK), for tests; returns its path."""
+    return _build(LIB_BOUNDS, BUILD_BOUNDS, force, False, ("-DDWT_BOUNDS_CHECK",))
+
+
+def _build(lib: str, build_dir: str, force: bool, verbose: bool, extra) -> str:
+    os.makedirs(build_dir, exist_ok=True)
+    if not force and not _stale(lib):
+        return lib
     srcs = sources()
     jobs = min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, list(extra), build_dir), srcs))
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print(LIB)
-    return LIB
+        print(lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -45,6 +45,7 @@ struct dwt2d_plan_s {
     int min_segq;
     // workspace layout (bytes from the start of the workspace)
     size_t off_a, off_b, off_x, off_y;
+    size_t size_a, size_b;  // bytes of the two LL buffers
     long long pitch_a, pitch_b, pitch_x;  // elements
     size_t ws_bytes;
     // profiling hook: events[2i] / events[2i+1] around launch i
@@ -279,6 +280,7 @@ dwt2d_status build_group(const dwt2d_plan_s* p, bool fwd, int k, const void* src
     const int rho = p->wavelet == DWT2D_CDF97 ? 2 : 1;
     void* bufs[2] = {ws + p->off_a, ws + p->off_b};
     const long long bpitch[2] = {p->pitch_a, p->pitch_b};
+    const long long belems[2] = {(long long)(p->size_a / p->elem), (long long)(p->size_b / p->elem)};
     FusedArgs& a = out->a;
     memset(&a, 0, sizeof(a));
     a.err = err;
@@ -295,9 +297,11 @@ dwt2d_status build_group(const dwt2d_plan_s* p, bool fwd, int k, const void* src
         const long long in_pitch = gi == 0 ? src_pe : bpitch[(gi - 1) & 1];
         a.mallat = dst;
         a.mallat_pitch = dst_pe;
+        a.mallat_elems = (long long)p->H * dst_pe;
         const bool last = gi == p->ngroups - 1;
         a.ll = last ? dst : bufs[gi & 1];
         a.ll_pitch = last ? dst_pe : bpitch[gi & 1];
+        a.ll_elems = last ? a.mallat_elems : belems[gi & 1];
         const int q1 = g.n >= 3 ? 4 : p->fwd_q1;
         dwt2d_status s = make_map(&out->m[0], in, a.lv[0].h, a.lv[0].w, in_pitch, p->elem, elem_kind,
                                   64 * q1);
@@ -338,6 +342,7 @@ dwt2d_status build_group(const dwt2d_plan_s* p, bool fwd, int k, const void* src
     const bool last = gi == 0;
     a.out = last ? dst : bufs[k & 1];
     a.out_pitch = last ? dst_pe : bpitch[k & 1];
+    a.out_elems = last ? (long long)p->H * dst_pe : belems[k & 1];
     out->nl = g.n;
     if (g.n <= 2) {
         // TMA ring: boxes of the Mallat array and of the LL source
@@ -687,8 +692,10 @@ static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width
     }
     p->off_a = take(ba);
     p->pitch_a = pa;
+    p->size_a = ba;
     p->off_b = take(bb);
     p->pitch_b = pb;
+    p->size_b = bb;
     if (multipass(scheme)) {
         const long long px = round_pitch(width + (width & 1), p->elem);
         const size_t bx = (size_t)px * (height + (height & 1)) * p->elem;
@@ -1164,6 +1171,7 @@ const char* dwt2d_status_string(dwt2d_status s) {
         case DWT2D_ERR_NOMEM: return "host allocation failed";
         case DWT2D_ERR_CUDA: return "CUDA error";
         case DWT2D_ERR_TIMEOUT: return "kernel wait timed out";
+        case DWT2D_ERR_BOUNDS: return "store out of bounds (bounds-checked build)";
     }
     return "unknown status";
 }

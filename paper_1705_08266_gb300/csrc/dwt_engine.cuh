@@ -80,6 +80,40 @@ struct Storage<__nv_bfloat16> {
     __device__ __forceinline__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
 };
 
+// Bounds-checked builds (-DDWT_BOUNDS_CHECK): every global store of the
+// streaming kernels is tested against the byte windows of the buffers the
+// warp may write (set per work item); a store outside them is skipped and
+// DWT2D_ERR_BOUNDS (-7) is recorded in the status word.
+struct StoreWindows {
+    const char* lo[2];
+    const char* hi[2];
+    int* err;
+};
+#ifdef DWT_BOUNDS_CHECK
+__shared__ StoreWindows g_store_windows[32];  // one per warp of the CTA
+__device__ __forceinline__ void set_store_windows(const void* b0, long long n0, const void* b1,
+                                                  long long n1, int* err) {
+    StoreWindows& w = g_store_windows[threadIdx.x >> 5];
+    w.lo[0] = static_cast<const char*>(b0);
+    w.hi[0] = w.lo[0] + n0;
+    w.lo[1] = static_cast<const char*>(b1);
+    w.hi[1] = w.lo[1] + n1;
+    w.err = err;
+}
+__device__ __forceinline__ bool store_ok(const void* p, int bytes) {
+    if (bytes <= 0) return true;  // nothing is written
+    const StoreWindows& w = g_store_windows[threadIdx.x >> 5];
+    const char* c = static_cast<const char*>(p);
+    for (int k = 0; k < 2; ++k)
+        if (w.lo[k] && c >= w.lo[k] && c + bytes <= w.hi[k]) return true;
+    atomicExch(w.err, -7);
+    return false;
+}
+#else
+__device__ __forceinline__ void set_store_windows(const void*, long long, const void*, long long, int*) {}
+__device__ __forceinline__ bool store_ok(const void*, int) { return true; }
+#endif
+
 // Raw vector of a given byte size (2, 4, 8 or 16).
 template <int BYTES>
 struct RawVec;

@@ -23,6 +23,7 @@ __device__ __forceinline__ void store_cols(S* p, const T (&v)[Q], int avail, boo
     S w[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) w[j] = Storage<S>::st(v[j]);
+    if (!store_ok(p, (avail < Q ? (avail > 0 ? avail : 0) : Q) * (int)sizeof(S))) return;
     if (vec && avail >= Q) {
         st_vec<S, Q>(p, w);
     } else {
@@ -312,6 +313,8 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArg
     W.e1.init();
     if constexpr (NL >= 2) W.e2.init();
     if constexpr (NL >= 3) W.e3.init();
+    set_store_windows(a.mallat, a.mallat_elems * (long long)sizeof(S), a.ll,
+                      a.ll_elems * (long long)sizeof(S), a.err);
 
     // ---- TMA ring prologue
     const uint32_t ring_s = smem_u32(ring);

@@ -35,6 +35,7 @@ struct FusedArgs {
     int nstrips, nsegs, segq;        // warp work items = nstrips * nsegs
     int seg_f;                       // segment order interleave (<= 1: top to bottom)
     int seg_lo;                      // first row segment of this launch (launches over a subset)
+    long long mallat_elems, ll_elems, out_elems;  // buffer extents (elements) for checked builds
     int valid_px, xoff;              // strip width in input pixels and left halo offset
     int lane_lo, lane_hi;            // lanes that store
     int* err;                        // device status word (0 = ok)

@@ -145,6 +145,7 @@ struct InvWarp {
         if (y >= out_h) return;
         const int x0 = xb + 8 * lane;
         T* p = out + (long long)y * out_pitch + x0;
+        if (!store_ok(p + max(-x0, 0), (min(x0 + 8, out_w) - max(x0, 0)) * (int)sizeof(T))) return;
         if (vec_out && x0 + 8 <= out_w) {
             using V = typename VecI<T, 4>::type;
             V w0, w1;
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(128) inv_fused_kernel(const FusedArgs a) {
     W.out_h = a.lv[0].h;
     W.out_w = a.lv[0].w;
     W.vec_out = (a.out_pitch % 4) == 0;
+    set_store_windows(a.out, a.out_elems * (long long)sizeof(T), nullptr, 0, a.err);
     const int ne1 = (a.lv[0].h + 1) >> 1;
     W.A0 = seg * a.segq;
     W.A1 = min(W.A0 + a.segq, ne1);

@@ -134,6 +134,8 @@ struct InvWarpT {
         S w[2 * Q1];
 #pragma unroll
         for (int j = 0; j < 2 * Q1; ++j) w[j] = Storage<S>::st(v[j]);
+        if (!store_ok(p + max(-x0l, 0), (min(x0l + 2 * Q1, out_w) - max(x0l, 0)) * (int)sizeof(S)))
+            return;
         if (vec_row) {
             st_vec<S, 2 * Q1>(p, w);
         } else {
@@ -185,6 +187,7 @@ __device__ __forceinline__ void inv_body(const CUtensorMap* m1p, const CUtensorM
     w.out_w = a.lv[0].w;
     w.vec_out = (a.out_pitch % (2 * Q1)) == 0;
     w.x0l = w.xb + 2 * Q1 * lane;
+    set_store_windows(a.out, a.out_elems * (long long)sizeof(S), nullptr, 0, a.err);
     w.vec_row = w.vec_out && w.x0l >= 0 && w.x0l + 2 * Q1 <= a.lv[0].w;
     const int ne1 = (a.lv[0].h + 1) >> 1;
     w.A0 = seg * a.segq;

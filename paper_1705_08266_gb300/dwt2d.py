@@ -17,7 +17,9 @@ from typing import Optional
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdwt2d.so")
+# DWT2D_LIBRARY selects another build of the same library (the bounds-checked
+# one in tests)
+LIB_PATH = os.environ.get("DWT2D_LIBRARY") or os.path.join(_HERE, "libdwt2d.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "dwt2d.h")
 
 WAVELETS = {"cdf97": 0, "legall53": 1}
@@ -32,7 +34,7 @@ SCHEMES = {
 }
 DTYPES = {torch.float32: 0, torch.int32: 1, torch.float16: 2, torch.bfloat16: 3}
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "alignment", -4: "no memory",
-          -5: "CUDA error", -6: "timeout"}
+          -5: "CUDA error", -6: "timeout", -7: "store out of bounds (checked build)"}
 
 _lib = None
 

@@ -89,7 +89,7 @@ def test_bad_pointers_rejected_without_gpu(L):
 
 
 def test_status_strings(L):
-    for s in (0, -1, -2, -3, -4, -5, -6):
+    for s in (0, -1, -2, -3, -4, -5, -6, -7):
         assert L.dwt2d_status_string(s)
 
 
