@@ -150,7 +150,9 @@ dwt2d_status dwt2d_inverse(dwt2d_plan_t plan, const void* d_src, int64_t src_pit
  *   by band as its input rows arrive, and the finished detail bands come back
  *   on a second internal stream while later bands still go in (the plan owns
  *   the two streams; a plan's _host calls must not overlap each other).  The
- *   inverse runs copy, transform, copy on `stream`.
+ *   inverse does the same the other way round: the coarse levels' top-left
+ *   region goes in first, the finest level group runs by row bands as their
+ *   detail bands arrive, and finished image rows come back meanwhile.
  *   d_stage_in, d_stage_out: device buffers of height rows x d_pitch_bytes.
  *   Errors: as dwt2d_forward, plus DWT2D_ERR_CUDA for a failed copy.
  */

@@ -877,6 +877,123 @@ static dwt2d_status run_host_fwd_pipelined(dwt2d_plan_s* p, const void* h_src, i
     return cudaStreamSynchronize(st) == cudaSuccess ? DWT2D_OK : DWT2D_ERR_CUDA;
 }
 
+// Host coefficients -> host image, the inverse counterpart: the top-left
+// region of the coarse levels goes in first and the coarse groups run on it;
+// the detail bands of the finest group's levels go in by row bands, that
+// group runs as launches over the row segments whose inputs have arrived, and
+// each launch's finished image rows go out while later bands come in.
+static dwt2d_status run_host_inv_pipelined(dwt2d_plan_s* p, const void* h_src, int64_t hsp,
+                                           void* h_dst, int64_t hdp, void* d_in, void* d_out,
+                                           int64_t dpitch, void* d_ws, cudaStream_t st) {
+    const int64_t es = p->elem;
+    const char* hs = reinterpret_cast<const char*>(h_src);
+    char* hd = reinterpret_cast<char*>(h_dst);
+    char* din = reinterpret_cast<char*>(d_in);
+    char* dout = reinterpret_cast<char*>(d_out);
+    char* wsb = reinterpret_cast<char*>(d_ws);
+    int* err = reinterpret_cast<int*>(wsb);
+    cudaEvent_t* ev = p->host_ev;  // [0] start, [1..8] bands in, [9..16] launches, [17] end
+    auto copy2d = [](char* dst, int64_t dp, const char* src, int64_t sp, int64_t w, int64_t rows,
+                     cudaMemcpyKind kind, cudaStream_t s) {
+        if (rows <= 0 || w <= 0) return cudaSuccess;
+        if (dp == w && sp == w) return cudaMemcpyAsync(dst, src, (size_t)(w * rows), kind, s);
+        return cudaMemcpy2DAsync(dst, dp, src, sp, w, rows, kind, s);
+    };
+    auto in_rows = [&](int r0, int r1, int c0, int c1) {  // coefficient rectangle, host -> device
+        return copy2d(din + r0 * dpitch + c0 * es, dpitch, hs + r0 * hsp + c0 * es, hsp,
+                      (int64_t)(c1 - c0) * es, r1 - r0, cudaMemcpyHostToDevice, p->host_in);
+    };
+    if (cudaEventRecord(ev[0], st) != cudaSuccess || cudaStreamWaitEvent(p->host_in, ev[0], 0) ||
+        cudaStreamWaitEvent(p->host_out, ev[0], 0))
+        return DWT2D_ERR_CUDA;
+    const int n0 = p->groups[0].n;  // levels of the finest group
+    const int hN = p->hs[n0 - 1], wN = p->ws[n0 - 1];
+    // the coarse region: levels > n0 and the last LL
+    if (in_rows(0, (hN + 1) / 2, 0, (wN + 1) / 2) != cudaSuccess) return DWT2D_ERR_CUDA;
+    // the finest group's detail bands by row bands of level-1 quadruple rows
+    const int ne_r1 = (p->hs[0] + 1) / 2;
+    const int unit = 1 << (n0 - 1);
+    const int rb = ((ne_r1 + kHostBands - 1) / kHostBands + unit - 1) / unit * unit;
+    for (int c = 0; c < kHostBands; ++c) {
+        for (int l = 0; l < n0; ++l) {
+            const int h = p->hs[l], w = p->ws[l];
+            const int ne_r = (h + 1) >> 1, no_r = h >> 1, ne_c = (w + 1) >> 1;
+            const int q0 = std::min((c * rb) >> l, ne_r);
+            const int q1 = c == kHostBands - 1 ? ne_r : std::min(((c + 1) * rb) >> l, ne_r);
+            if (q1 <= q0) continue;
+            if (in_rows(q0, q1, ne_c, w) != cudaSuccess) return DWT2D_ERR_CUDA;  // HL
+            const int r1 = std::min(q1, no_r);
+            if (r1 > q0 && in_rows(ne_r + q0, ne_r + r1, 0, w) != cudaSuccess) return DWT2D_ERR_CUDA;
+        }
+        if (cudaEventRecord(ev[1 + c], p->host_in) != cudaSuccess) return DWT2D_ERR_CUDA;
+    }
+    const int elem_kind = elem_kind_of(p->dtype);
+    const int sch = base_scheme(p->scheme);
+    const int G = p->ngroups;
+    // coarse groups: their input (the coarse region) went in first
+    if (G > 1 && cudaStreamWaitEvent(st, ev[1], 0) != cudaSuccess) return DWT2D_ERR_CUDA;
+    for (int k = 0; k + 1 < G; ++k) {
+        GroupLaunch gl;
+        dwt2d_status s = build_group(p, false, k, d_in, dpitch / es, d_out, dpitch / es, wsb, err,
+                                     p->fwd_warps_target, p->inv_warps_target, &gl);
+        if (s != DWT2D_OK) return s;
+        const cudaError_t e = gl.path == 1 ? launch_inv_tma(elem_kind, sch, gl.nl, gl.q1, gl.m[0], gl.m[1],
+                                                            gl.m[2], gl.a, gl.grid, st)
+                                           : launch_inv_fused(elem_kind, sch, gl.nl, gl.a, gl.grid, st);
+        if (e != cudaSuccess) return DWT2D_ERR_CUDA;
+    }
+    GroupLaunch gf;
+    dwt2d_status s = build_group(p, false, G - 1, d_in, dpitch / es, d_out, dpitch / es, wsb, err,
+                                 p->fwd_warps_target, p->inv_warps_target, &gf);
+    if (s != DWT2D_OK) return s;
+    if (gf.path != 1) return DWT2D_ERR_INVALID;
+    FusedArgs base = gf.a;
+    base.seg_f = 1;
+    const int lag = p->wavelet == DWT2D_CDF97 ? 2 : 1;
+    const int pro_slots = n0 == 2 ? lag : 0;
+    const int ne_r2 = n0 == 2 ? (p->hs[1] + 1) / 2 : 0;
+    auto ready = [&](int seg, int c) {  // rows segment `seg` reads are all in after band c
+        if (c == kHostBands - 1) return true;
+        const int A0 = seg * base.segq, A1 = std::min(A0 + base.segq, ne_r1);
+        const int qstart = std::max(A0 - lag, 0) & ~3;
+        const int nmain = (A1 + lag - qstart + 3) / 4;
+        const int end1 = std::min(qstart + 4 * nmain, ne_r1);
+        if (end1 > std::min((c + 1) * rb, ne_r1)) return false;
+        if (n0 == 2) {
+            const int qlast = qstart - 4 * pro_slots + 4 * (nmain + pro_slots - 1);
+            const int end2 = std::min(qlast / 2 + lag + 2, ne_r2);
+            if (end2 > std::min(((c + 1) * rb) >> 1, ne_r2)) return false;
+        }
+        return true;
+    };
+    int next = 0;
+    for (int c = 0; c < kHostBands && next < base.nsegs; ++c) {
+        int end = next;
+        while (end < base.nsegs && ready(end, c)) ++end;
+        if (end == next) continue;
+        FusedArgs a = base;
+        a.seg_lo = next;
+        a.nsegs = end - next;
+        const int grid = (a.nstrips * a.nsegs + kInvTmaWarps - 1) / kInvTmaWarps;
+        if (cudaStreamWaitEvent(st, ev[1 + c], 0) != cudaSuccess ||
+            launch_inv_tma(elem_kind, sch, gf.nl, gf.q1, gf.m[0], gf.m[1], gf.m[2], a, grid, st) !=
+                cudaSuccess ||
+            cudaEventRecord(ev[9 + c], st) != cudaSuccess ||
+            cudaStreamWaitEvent(p->host_out, ev[9 + c], 0) != cudaSuccess)
+            return DWT2D_ERR_CUDA;
+        const int y0 = std::min(2 * next * base.segq, p->H);
+        const int y1 = std::min(2 * std::min(end * base.segq, ne_r1), p->H);
+        if (copy2d(hd + y0 * hdp, hdp, dout + y0 * dpitch, dpitch, (int64_t)p->W * es, y1 - y0,
+                   cudaMemcpyDeviceToHost, p->host_out) != cudaSuccess)
+            return DWT2D_ERR_CUDA;
+        next = end;
+    }
+    if (cudaStreamWaitEvent(st, ev[kHostBands], 0) != cudaSuccess ||
+        cudaEventRecord(ev[17], p->host_out) != cudaSuccess || cudaStreamWaitEvent(st, ev[17], 0))
+        return DWT2D_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? DWT2D_OK : DWT2D_ERR_CUDA;
+}
+
 static dwt2d_status run_host(dwt2d_plan_t p, bool fwd, const void* h_src, int64_t hsp, void* h_dst,
                              int64_t hdp, void* d_in, void* d_out, int64_t dpitch, void* d_ws,
                              float scale, void* stream) {
@@ -889,6 +1006,10 @@ static dwt2d_status run_host(dwt2d_plan_t p, bool fwd, const void* h_src, int64_
                                                       DWT2D_OK &&
         p->groups[0].n <= 2 && scale_ok(p, scale) && host_resources(p))
         return run_host_fwd_pipelined(p, h_src, hsp, h_dst, hdp, d_in, d_out, dpitch, d_ws, st);
+    if (!fwd && p->H >= 1024 && !multipass(p->scheme) && env_int("DWT2D_HOST_PIPELINE", 1) != 0 &&
+        check_buffers(p, d_in, dpitch, d_out, dpitch, d_ws) == DWT2D_OK && p->groups[0].n <= 2 &&
+        p->inv_q1 == 2 && scale_ok(p, scale) && host_resources(p))
+        return run_host_inv_pipelined(p, h_src, hsp, h_dst, hdp, d_in, d_out, dpitch, d_ws, st);
     // one linear copy when both sides are unpadded (faster than a 2-D copy)
     auto copy = [&](void* dst, int64_t dp, const void* src, int64_t sp, cudaMemcpyKind kind) {
         if (dp == row && sp == row)

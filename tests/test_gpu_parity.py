@@ -143,9 +143,10 @@ def test_host_entry_points():
     (1030, 2050, 5, "cdf97", torch.float32), (2048, 1536, 3, "legall53", torch.int32),
     (4097, 333, 2, "cdf97", torch.float32), (1024, 1024, 1, "cdf97", torch.float32),
     (1500, 900, 6, "cdf97", torch.float16), (3001, 777, 4, "legall53", torch.int32)])
-def test_host_forward_pipelined_equals_device_forward(h, w, levels, wavelet, dtype):
-    """The host-buffer forward overlaps its copies with the transform by row
-    bands; the coefficients are the device entry point's, bit for bit."""
+def test_host_pipelined_equals_device_entry_points(h, w, levels, wavelet, dtype):
+    """The host-buffer forward and inverse overlap their copies with the
+    transform by row bands; the results are the device entry points', bit for
+    bit."""
     x = make_input(wavelet, h, w, seed=h + w)
     if dtype == torch.float16:
         x = x / float(np.max(np.abs(x)))
@@ -160,6 +161,13 @@ def test_host_forward_pipelined_equals_device_forward(h, w, levels, wavelet, dty
     ref = plan.forward(device_image(x).to(dtype) if dtype != torch.float16 else _dev16(xt))
     torch.cuda.synchronize()
     assert torch.equal(hd, ref.cpu())
+    assert plan.status(ws) == 0
+    # the inverse counterpart (coarse region first, detail bands by rows, image rows out)
+    back = torch.full_like(hs, 5).pin_memory()
+    plan.inverse_host(hd, back, din, dout, ws)
+    ref_back = plan.inverse(_dev16(hd))
+    torch.cuda.synchronize()
+    assert torch.equal(back, ref_back.cpu())
     assert plan.status(ws) == 0
 
 
