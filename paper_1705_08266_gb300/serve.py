@@ -249,6 +249,18 @@ class Server:
                 time.sleep(sleep)
         return False
 
+    def result(self, t: Ticket, timeout: float = 60.0) -> torch.Tensor:
+        """Drive the loop until `t` finishes; its resident result, or raise
+        with the reason it did not complete."""
+        t_end = self.clock() + timeout
+        while not t.finished():
+            if self.clock() >= t_end:
+                raise TimeoutError(f"request {t.id} still {t.state} after {timeout} s")
+            self.poll()
+        if t.state != DONE:
+            raise RuntimeError(f"request {t.id} {t.state}: {t.error}")
+        return t.result
+
     def stats(self) -> dict:
         done = [t for t in self.finished if t.state == DONE]
         lat = sorted(t.latency for t in done)

@@ -214,3 +214,16 @@ def test_non_pitched_input_is_copied_and_counted():
     assert srv.run_until_idle(5)
     assert torch.equal(t.result, 2 * x)
     assert srv.in_use == img_bytes(8, 8)
+
+
+def test_result_drives_the_loop_and_reports_failures():
+    srv = S.Server(budget_bytes=1 << 30, executor=FakeExecutor(lag=2))
+    t = srv.submit(req(fill=2.0))
+    assert torch.all(srv.result(t, timeout=5) == 4.0)
+    bad = srv.submit(S.Request(8, 8, 0, data=torch.zeros(8, 8)))
+    with pytest.raises(RuntimeError, match="rejected"):
+        srv.result(bad, timeout=5)
+    slow = srv.submit(S.Request(8, 8, 2, loader=lambda: (time.sleep(0.5), torch.zeros(8, 8))[1]))
+    with pytest.raises(TimeoutError):
+        srv.result(slow, timeout=0.05)
+    assert torch.all(srv.result(slow, timeout=5) == 0.0)
