@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--inverse-only", action="store_true",
+                    help="time only the inverse of the headline workload (for profiling its kernels)")
     ap.add_argument("--size", type=int, default=8192,
                     help="image side (profiling runs use a smaller case; the metric is 8192)")
     return ap.parse_args()
@@ -270,6 +272,9 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.inverse_only:
+        inverse_only(args, D, synth, dev)
+        return
     x_h = synth.gradient_noise(H, W, synth.SEED_LARGE)
     x = D.empty_image(H, W, torch.float32, dev)
     x.copy_(torch.from_numpy(x_h))
@@ -388,6 +393,28 @@ def main():
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def inverse_only(args, D, synth, dev):
+    """The inverse of the headline workload alone: warm-up, then K timed steps
+    (one line of JSON with the per-step time), for profiling its launches."""
+    x = D.empty_image(H, W, torch.float32, dev)
+    x.copy_(torch.from_numpy(synth.gradient_noise(H, W, synth.SEED_LARGE)))
+    c = D.empty_image(H, W, torch.float32, dev)
+    y = D.empty_image(H, W, torch.float32, dev)
+    plan = D.Plan(H, W, LEVELS, "cdf97", HEADLINE_SCHEME)
+    wsb = plan.workspace(dev)
+    stream = torch.cuda.Stream(dev)
+    plan.forward(x, c, wsb, stream=stream)
+    inv = lambda: plan.inverse(c, y, wsb, stream=stream)  # noqa: E731
+    for _ in range(max(args.warmup, 3)):
+        inv()
+    K = max(args.steps, 1)
+    ms = time_calls(inv, K, stream)
+    assert plan.status(wsb) == 0, "kernel reported a timeout"
+    print(json.dumps({"inverse_ms_per_step": round(ms, 5), "image": [H, W], "levels": LEVELS,
+                      "scheme": HEADLINE_SCHEME, "launches_per_step": plan.info()[0], "steps": K}),
+          flush=True)
 
 
 def variants(D, synth, dev, stream, x, dst):
