@@ -643,10 +643,10 @@ static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width
                              ? 0
                              : sms * env_int("DWT2D_FWD_WARPS_PER_SM_LARGE", 44);
     p->large_segq = env_int("DWT2D_LARGE_SEGQ", 16);
-    // the finest inverse launch: about 24 warps per SM (2 waves of 12)
+    // the finest inverse launch: about 48 warps per SM (3 waves of 16)
     p->inv_warps_large = tuning && tuning->warps_per_sm > 0
                              ? 0
-                             : sms * env_int("DWT2D_INV_WARPS_PER_SM_LARGE", 24);
+                             : sms * env_int("DWT2D_INV_WARPS_PER_SM_LARGE", 48);
     p->fwd_q1 = env_int("DWT2D_FWD_Q", 2) == 4 && !half ? 4 : 2;
     p->inv_q1 = env_int("DWT2D_INV_Q", 2) == 4 && !half ? 4 : 2;
 

@@ -291,9 +291,9 @@ __device__ __forceinline__ void inv_body(const CUtensorMap* m1p, const CUtensorM
     }
 }
 
-// 12 warps per SM (168 registers) with 2 quadruple columns per lane, 8 with 4
+// 16 warps per SM (128 registers) with 2 quadruple columns per lane, 8 with 4
 template <class S, int SCH, int NL, int Q1>
-__global__ void __launch_bounds__(kInvWarps * 32, (Q1 <= 2 ? 12 : 8) / kInvWarps)
+__global__ void __launch_bounds__(kInvWarps * 32, (Q1 <= 2 ? 16 : 8) / kInvWarps)
     inv_tma_kernel(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2,
                    const __grid_constant__ CUtensorMap ml, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(kInvWarps * 32, (Q1 <= 2 ? 12 : 8) / kInvWarps
     inv_body<S, SCH, NL, Q1>(&m1, &m2, &ml, a, wid, smem_raw);
 }
 
+// arguments in registers (not the constant bank): 12 warps per SM, no spills
 template <class S, int SCH, int NL, int Q1>
 __global__ void __launch_bounds__(kInvWarps * 32, (Q1 <= 2 ? 12 : 8) / kInvWarps)
     inv_batched_kernel(const BatchEntry* __restrict__ table, int n) {
