@@ -291,9 +291,12 @@ __device__ __forceinline__ void inv_body(const CUtensorMap* m1p, const CUtensorM
     }
 }
 
-// 16 warps per SM (128 registers) with 2 quadruple columns per lane, 8 with 4
+// 16 warps per SM (128 registers) with 2 quadruple columns per lane, 8 with 4;
+// the plain non-separable steps (48 multiply-adds per quadruple) measured
+// faster with the register budget of 12 warps
 template <class S, int SCH, int NL, int Q1>
-__global__ void __launch_bounds__(kInvWarps * 32, (Q1 <= 2 ? 16 : 8) / kInvWarps)
+__global__ void __launch_bounds__(kInvWarps * 32,
+                                  (Q1 <= 2 ? (SCH == SCH_NONSEP ? 12 : 16) : 8) / kInvWarps)
     inv_tma_kernel(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2,
                    const __grid_constant__ CUtensorMap ml, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
