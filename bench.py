@@ -585,15 +585,18 @@ def serving_variant(D, synth, dev, seconds: float = 10.0, rate: float = 2000.0):
         wav, dt = ("cdf97", torch.float16) if rng.random() < 0.5 else ("legall53", torch.int32)
         reqs.append(S.Request(h, w, lv, wav, dt, inv, data=base[dt][:h, :w]))
         px += h * w
+    import gc
+
     srv = S.Server(budget_bytes=40 << 30, device=dev)
     # warm-up: module loading and kernel attributes outside the measurement
-    for r in reqs[:32]:
-        srv.submit(r)
+    warm = [srv.submit(r) for r in reqs[:32]]
     srv.run_until_idle(60)
-    for t in list(srv.finished):
+    for t in warm:
         srv.release(t)
-    srv.finished.clear()
-    tickets = []
+    srv.reset_stats()
+    # no collector pauses inside the timed loop (a serving process would tune it too)
+    gc.collect()
+    gc.disable()
     t0 = time.perf_counter()
     i = 0
     pending = []
@@ -607,11 +610,11 @@ def serving_variant(D, synth, dev, seconds: float = 10.0, rate: float = 2000.0):
         for t in pending:
             if t.finished():
                 srv.release(t)
-                tickets.append(t)
             else:
                 still.append(t)
         pending = still
     wall = time.perf_counter() - t0
+    gc.enable()
     st = srv.stats()
     srv.close()
     return {"workload": "Poisson 2000/s for 10 s; s log-uniform [64, 8192], aspect U[1,4], short side "

@@ -172,8 +172,9 @@ class Server:
         self.peak = 0
         self.queue: List[Ticket] = []
         self.inflight = []  # (handle, [tickets])
-        self.tickets = {}
-        self.finished: List[Ticket] = []
+        # finished requests are counted, not kept (the client holds its tickets)
+        self.counts = {DONE: 0, FAILED: 0, CANCELLED: 0, REJECTED: 0}
+        self.latencies: List[float] = []
         self._ids = itertools.count()
         self._lock = threading.Lock()
         self._loaders = cf.ThreadPoolExecutor(max_workers=loader_threads)
@@ -184,7 +185,6 @@ class Server:
     def submit(self, req: Request, t_arrival: Optional[float] = None) -> Ticket:
         """Queue a request (latency counts from t_arrival, default now)."""
         t = Ticket(next(self._ids), req, t_submit=self.clock() if t_arrival is None else t_arrival)
-        self.tickets[t.id] = t
         why = validate(req)
         if not why:
             try:
@@ -262,21 +262,25 @@ class Server:
         return t.result
 
     def stats(self) -> dict:
-        done = [t for t in self.finished if t.state == DONE]
-        lat = sorted(t.latency for t in done)
+        lat = sorted(self.latencies)
 
         def q(p):
             if not lat:
                 return None
             return lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))]
 
-        count = {s: 0 for s in (DONE, FAILED, CANCELLED, REJECTED)}
-        for t in self.finished:
-            count[t.state] = count.get(t.state, 0) + 1
-        return {"completed": count[DONE], "failed": count[FAILED], "cancelled": count[CANCELLED],
-                "rejected": count[REJECTED], "p50_s": q(0.50), "p99_s": q(0.99),
+        c = self.counts
+        return {"completed": c[DONE], "failed": c[FAILED], "cancelled": c[CANCELLED],
+                "rejected": c[REJECTED], "p50_s": q(0.50), "p99_s": q(0.99),
                 "max_s": lat[-1] if lat else None, "batches": self.batches,
                 "peak_bytes": self.peak, "budget_bytes": self.budget}
+
+    def reset_stats(self):
+        """Forget the counts and latencies so far (e.g. after a warm-up)."""
+        self.counts = {k: 0 for k in self.counts}
+        self.latencies = []
+        self.batches = 0
+        self.peak = self.in_use
 
     def close(self):
         self._loaders.shutdown(wait=True)
@@ -328,7 +332,9 @@ class Server:
         if state != DONE:
             t.result = None
             t._src = None
-        self.finished.append(t)
+        self.counts[state] = self.counts.get(state, 0) + 1
+        if state == DONE:
+            self.latencies.append(t.t_done - t.t_submit)
         t._event.set()
 
     def admit_and_launch(self):
