@@ -43,6 +43,7 @@ struct dwt2d_plan_s {
     int fwd_q1;  // quadruple columns per lane of the forward kernel (2 or 4)
     int inv_q1;  // the same for the inverse
     int min_segq;
+    int pdl;  // device entry points: launches with programmatic stream serialization
     // workspace layout (bytes from the start of the workspace)
     size_t off_a, off_b, off_x, off_y;
     size_t size_a, size_b;  // bytes of the two LL buffers
@@ -65,6 +66,7 @@ struct dwt2d_batch_s {
         int grid;
     };
     dwt2d_scheme scheme;
+    bool pdl;  // launches with programmatic stream serialization
     std::vector<dwt2d_batch_item> items;
     std::vector<dwt2d_plan_s*> plans;
     std::vector<size_t> region;             // workspace offset of each image's LL buffers
@@ -390,6 +392,7 @@ dwt2d_status run_fused(const dwt2d_plan_s* p, bool fwd, const void* src, int64_t
         dwt2d_status s = build_group(p, fwd, k, src, sp / p->elem, dst, dp / p->elem, wsb, err,
                                      p->fwd_warps_target, p->inv_warps_target, &gl);
         if (s != DWT2D_OK) return s;
+        gl.a.pdl = p->pdl;
         cudaError_t e;
         mark(p, k, 0, st);
         if (gl.path == 0)
@@ -648,6 +651,7 @@ static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width
                              ? 0
                              : sms * env_int("DWT2D_INV_WARPS_PER_SM_LARGE", 48);
     p->fwd_q1 = env_int("DWT2D_FWD_Q", 2) == 4 && !half ? 4 : 2;
+    p->pdl = env_int("DWT2D_PDL", 1) != 0;
     p->inv_q1 = env_int("DWT2D_INV_Q", 2) == 4 && !half ? 4 : 2;
 
     // workspace: header | LL buffer A | LL buffer B | (multipass) X | Y
@@ -1116,6 +1120,7 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
     dwt2d_batch_s* b = new (std::nothrow) dwt2d_batch_s();
     if (!b) return DWT2D_ERR_NOMEM;
     b->scheme = scheme;
+    b->pdl = env_int("DWT2D_BATCH_PDL", 0) != 0;  // measured neutral to 1 % slower for batches
     b->items.assign(items, items + n);
     size_t off = kHeader;
     b->table_off = off;
@@ -1245,8 +1250,8 @@ dwt2d_status dwt2d_batch_upload(dwt2d_batch_t b, void* d_ws, void* stream) {
         }
         // kernel attributes once, outside any capture
         const int sch = base_scheme(b->scheme);
-        const cudaError_t e = L.fwd ? launch_fwd_batched(L.elem_kind, sch, L.nl, nullptr, 0, 0, st)
-                                    : launch_inv_batched(L.elem_kind, sch, L.nl, nullptr, 0, 0, st);
+        const cudaError_t e = L.fwd ? launch_fwd_batched(L.elem_kind, sch, L.nl, nullptr, 0, 0, st, false)
+                                    : launch_inv_batched(L.elem_kind, sch, L.nl, nullptr, 0, 0, st, false);
         if (e != cudaSuccess) return DWT2D_ERR_CUDA;
     }
     if (!b->table.empty() &&
@@ -1267,8 +1272,8 @@ dwt2d_status dwt2d_batch_launch(dwt2d_batch_t b, void* d_ws, void* stream) {
     const int sch = base_scheme(b->scheme);
     for (const auto& L : b->launches) {
         const cudaError_t e =
-            L.fwd ? launch_fwd_batched(L.elem_kind, sch, L.nl, table + L.first, L.count, L.grid, st)
-                  : launch_inv_batched(L.elem_kind, sch, L.nl, table + L.first, L.count, L.grid, st);
+            L.fwd ? launch_fwd_batched(L.elem_kind, sch, L.nl, table + L.first, L.count, L.grid, st, b->pdl)
+                  : launch_inv_batched(L.elem_kind, sch, L.nl, table + L.first, L.count, L.grid, st, b->pdl);
         if (e != cudaSuccess) return DWT2D_ERR_CUDA;
     }
     return DWT2D_OK;

@@ -365,6 +365,7 @@ template <class S, int SCH, int NL, int Q1>
 __global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
     fwd_fused_kernel(const __grid_constant__ CUtensorMap map, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    grid_dependency_sync();
     const int wid = blockIdx.x * kFwdWarps + (threadIdx.x >> 5);
     if (wid >= a.nstrips * a.nsegs) return;
     fwd_body<S, SCH, NL, Q1>(&map, a, wid, smem_raw);
@@ -378,6 +379,7 @@ template <class S, int SCH, int NL, int Q1>
 __global__ void __launch_bounds__(kFwdWarps * 32, 12 / kFwdWarps)
     fwd_batched_kernel(const BatchEntry* __restrict__ table, int n) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    grid_dependency_sync();
     const int gw = blockIdx.x * kFwdWarps + (threadIdx.x >> 5);
     int lo = 0, hi = n - 1;  // last entry with first <= gw
     while (lo < hi) {
@@ -405,42 +407,41 @@ static cudaError_t launch_one(const CUtensorMap& map, const FusedArgs& a, int gr
     const size_t smem = fwd_smem_bytes(sizeof(S), Q1);
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k<<<grid, kFwdWarps * 32, smem, st>>>(map, a);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, kFwdWarps * 32, smem, st, a.pdl != 0, map, a);
 }
 
 template <class S, int SCH, int NL>
-static cudaError_t launch_batched_one(const BatchEntry* table, int n, int grid, cudaStream_t st) {
+static cudaError_t launch_batched_one(const BatchEntry* table, int n, int grid, cudaStream_t st,
+                                      bool pdl) {
     auto k = fwd_batched_kernel<S, SCH, NL, 2>;
     const size_t smem = fwd_smem_bytes(sizeof(S), 2);
     if (grid == 0)
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<grid, kFwdWarps * 32, smem, st>>>(table, n);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, kFwdWarps * 32, smem, st, pdl, table, n);
 }
 
 template <class S>
 static cudaError_t launch_batched_s(int sch, int nl, const BatchEntry* table, int n, int grid,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, bool pdl) {
     if (nl < 1 || nl > 2) return cudaErrorInvalidValue;
     switch (sch) {
-        case SCH_SEP: return nl == 1 ? launch_batched_one<S, SCH_SEP, 1>(table, n, grid, st)
-                                     : launch_batched_one<S, SCH_SEP, 2>(table, n, grid, st);
-        case SCH_NONSEP: return nl == 1 ? launch_batched_one<S, SCH_NONSEP, 1>(table, n, grid, st)
-                                        : launch_batched_one<S, SCH_NONSEP, 2>(table, n, grid, st);
-        case SCH_RED: return nl == 1 ? launch_batched_one<S, SCH_RED, 1>(table, n, grid, st)
-                                     : launch_batched_one<S, SCH_RED, 2>(table, n, grid, st);
+        case SCH_SEP: return nl == 1 ? launch_batched_one<S, SCH_SEP, 1>(table, n, grid, st, pdl)
+                                     : launch_batched_one<S, SCH_SEP, 2>(table, n, grid, st, pdl);
+        case SCH_NONSEP: return nl == 1 ? launch_batched_one<S, SCH_NONSEP, 1>(table, n, grid, st, pdl)
+                                        : launch_batched_one<S, SCH_NONSEP, 2>(table, n, grid, st, pdl);
+        case SCH_RED: return nl == 1 ? launch_batched_one<S, SCH_RED, 1>(table, n, grid, st, pdl)
+                                     : launch_batched_one<S, SCH_RED, 2>(table, n, grid, st, pdl);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fwd_batched(int elem, int scheme, int nl, const BatchEntry* table, int n, int grid,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool pdl) {
     switch (elem) {
-        case 0: return launch_batched_s<float>(scheme, nl, table, n, grid, st);
-        case 1: return launch_batched_s<int>(scheme, nl, table, n, grid, st);
-        case 2: return launch_batched_s<__half>(scheme, nl, table, n, grid, st);
-        case 3: return launch_batched_s<__nv_bfloat16>(scheme, nl, table, n, grid, st);
+        case 0: return launch_batched_s<float>(scheme, nl, table, n, grid, st, pdl);
+        case 1: return launch_batched_s<int>(scheme, nl, table, n, grid, st, pdl);
+        case 2: return launch_batched_s<__half>(scheme, nl, table, n, grid, st, pdl);
+        case 3: return launch_batched_s<__nv_bfloat16>(scheme, nl, table, n, grid, st, pdl);
     }
     return cudaErrorInvalidValue;
 }

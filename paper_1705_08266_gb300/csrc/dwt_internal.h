@@ -39,6 +39,7 @@ struct FusedArgs {
     int valid_px, xoff;              // strip width in input pixels and left halo offset
     int lane_lo, lane_hi;            // lanes that store
     int* err;                        // device status word (0 = ok)
+    int pdl;                         // host: launch with programmatic stream serialization
 };
 
 // Where a multipass kernel reads or writes a level's coefficients.
@@ -84,9 +85,29 @@ size_t fwd_smem_bytes(int elem_bytes, int q1);
 // grid == 0 only sets the kernel's shared-memory attribute (done once, before
 // any stream capture), so a launch itself is a plain kernel launch.
 cudaError_t launch_fwd_batched(int elem, int scheme, int nl, const BatchEntry* table, int n, int grid,
-                               cudaStream_t st);
+                               cudaStream_t st, bool pdl);
 cudaError_t launch_inv_batched(int elem, int scheme, int nl, const BatchEntry* table, int n, int grid,
-                               cudaStream_t st);
+                               cudaStream_t st, bool pdl);
+
+// Launch `kernel` on `st`; with `pdl` the grid is launched with programmatic
+// stream serialization (it may be scheduled while the previous kernel in the
+// stream drains, and waits in griddepcontrol.wait before its first global
+// access).  Only kernels that issue that wait may be launched with `pdl`.
+template <class... P, class... A>
+cudaError_t launch_kernel(void (*kernel)(P...), int grid, int block, size_t smem, cudaStream_t st,
+                          bool pdl, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
 
 // q1: quadruple columns per lane at the first fused level (2 or 4; 3 fused levels need 4)
 cudaError_t launch_fwd_fused(int elem, int scheme, int nl, int q1, const CUtensorMap& map,

@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(kInvWarps * 32,
     inv_tma_kernel(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2,
                    const __grid_constant__ CUtensorMap ml, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    grid_dependency_sync();
     const int wid = blockIdx.x * kInvWarps + (threadIdx.x >> 5);
     if (wid >= a.nstrips * a.nsegs) return;
     inv_body<S, SCH, NL, Q1>(&m1, &m2, &ml, a, wid, smem_raw);
@@ -310,6 +311,7 @@ template <class S, int SCH, int NL, int Q1>
 __global__ void __launch_bounds__(kInvWarps * 32, (Q1 <= 2 ? 12 : 8) / kInvWarps)
     inv_batched_kernel(const BatchEntry* __restrict__ table, int n) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    grid_dependency_sync();
     const int gw = blockIdx.x * kInvWarps + (threadIdx.x >> 5);
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -343,8 +345,7 @@ static cudaError_t inv_launch_one(const CUtensorMap& m1, const CUtensorMap& m2,
     const size_t smem = inv_tma_smem_bytes(sizeof(S), NL, Q1);
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k<<<grid, kInvWarps * 32, smem, st>>>(m1, m2, ml, a);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, kInvWarps * 32, smem, st, a.pdl != 0, m1, m2, ml, a);
 }
 
 template <class T, int SCH>
@@ -379,37 +380,37 @@ static cudaError_t inv_launch_sch(int sch, int nl, int q1, const CUtensorMap& m1
 }
 
 template <class S, int SCH, int NL>
-static cudaError_t inv_batched_one(const BatchEntry* table, int n, int grid, cudaStream_t st) {
+static cudaError_t inv_batched_one(const BatchEntry* table, int n, int grid, cudaStream_t st,
+                                   bool pdl) {
     auto k = inv_batched_kernel<S, SCH, NL, 2>;
     const size_t smem = inv_tma_smem_bytes(sizeof(S), NL, 2);
     if (grid == 0)
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<grid, kInvWarps * 32, smem, st>>>(table, n);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, kInvWarps * 32, smem, st, pdl, table, n);
 }
 
 template <class S>
 static cudaError_t inv_batched_s(int sch, int nl, const BatchEntry* table, int n, int grid,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, bool pdl) {
     if (nl < 1 || nl > 2) return cudaErrorInvalidValue;
     switch (sch) {
-        case SCH_SEP: return nl == 1 ? inv_batched_one<S, SCH_SEP, 1>(table, n, grid, st)
-                                     : inv_batched_one<S, SCH_SEP, 2>(table, n, grid, st);
-        case SCH_NONSEP: return nl == 1 ? inv_batched_one<S, SCH_NONSEP, 1>(table, n, grid, st)
-                                        : inv_batched_one<S, SCH_NONSEP, 2>(table, n, grid, st);
-        case SCH_RED: return nl == 1 ? inv_batched_one<S, SCH_RED, 1>(table, n, grid, st)
-                                     : inv_batched_one<S, SCH_RED, 2>(table, n, grid, st);
+        case SCH_SEP: return nl == 1 ? inv_batched_one<S, SCH_SEP, 1>(table, n, grid, st, pdl)
+                                     : inv_batched_one<S, SCH_SEP, 2>(table, n, grid, st, pdl);
+        case SCH_NONSEP: return nl == 1 ? inv_batched_one<S, SCH_NONSEP, 1>(table, n, grid, st, pdl)
+                                        : inv_batched_one<S, SCH_NONSEP, 2>(table, n, grid, st, pdl);
+        case SCH_RED: return nl == 1 ? inv_batched_one<S, SCH_RED, 1>(table, n, grid, st, pdl)
+                                     : inv_batched_one<S, SCH_RED, 2>(table, n, grid, st, pdl);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_inv_batched(int elem, int scheme, int nl, const BatchEntry* table, int n, int grid,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool pdl) {
     switch (elem) {
-        case 0: return inv_batched_s<float>(scheme, nl, table, n, grid, st);
-        case 1: return inv_batched_s<int>(scheme, nl, table, n, grid, st);
-        case 2: return inv_batched_s<__half>(scheme, nl, table, n, grid, st);
-        case 3: return inv_batched_s<__nv_bfloat16>(scheme, nl, table, n, grid, st);
+        case 0: return inv_batched_s<float>(scheme, nl, table, n, grid, st, pdl);
+        case 1: return inv_batched_s<int>(scheme, nl, table, n, grid, st, pdl);
+        case 2: return inv_batched_s<__half>(scheme, nl, table, n, grid, st, pdl);
+        case 3: return inv_batched_s<__nv_bfloat16>(scheme, nl, table, n, grid, st, pdl);
     }
     return cudaErrorInvalidValue;
 }

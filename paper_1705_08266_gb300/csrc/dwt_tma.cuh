@@ -75,6 +75,18 @@ __device__ __forceinline__ void fence_tensormap_acquire(const CUtensorMap* map) 
                  : "memory");
 }
 
+// Programmatic dependent launch.  A grid launched with programmatic stream
+// serialization may become resident while the kernel before it in the stream
+// is still draining; griddepcontrol.wait blocks the calling thread until every
+// prerequisite grid has completed and its memory is visible (it returns at
+// once for a grid launched without the attribute).  launch_dependents lets the
+// next such grid be scheduled once every CTA of this one has issued it or
+// exited.  Both are issued by every thread before its first global access.
+__device__ __forceinline__ void grid_dependency_sync() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // About one second at GB300 clocks.
 constexpr long long kWaitBudget = 2000000000LL;
 

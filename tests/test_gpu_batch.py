@@ -221,3 +221,33 @@ def test_autotune_picks_a_candidate_and_caches(tmp_path):
     torch.cuda.synchronize()
     assert b.status(ws) == 0
     _assert_same_as_single(jobs, "nonsep_reduced", "autotuned")
+
+
+def test_programmatic_batch_launch_changes_nothing(monkeypatch):
+    """Batched launches with programmatic stream serialization (off by
+    default), eager and replayed from a CUDA graph: the same bits as the
+    serialized launches."""
+    out = {}
+    for pdl in ("0", "1"):
+        monkeypatch.setenv("DWT2D_BATCH_PDL", pdl)
+        jobs, _ = _jobs(MIXED, 555)
+        batch = D.Batch(jobs)
+        ws = batch.workspace()
+        side = torch.cuda.Stream()
+        batch.upload(ws, stream=side)
+        for _ in range(3):
+            batch.launch(ws, stream=side)
+        side.synchronize()
+        eager = [dst.cpu() for (_s, dst, _l, _w, _i) in jobs]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            batch.launch(ws, stream=side)
+        for (_s, dst, _l, _w, _i) in jobs:
+            dst.fill_(0)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert batch.status(ws) == 0
+        out[pdl] = (eager, [dst.cpu() for (_s, dst, _l, _w, _i) in jobs])
+    for a, b in zip(out["0"][0] + out["0"][1], out["1"][0] + out["1"][1]):
+        assert torch.equal(a, b)

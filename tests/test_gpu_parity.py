@@ -199,3 +199,38 @@ def test_cross_scheme_agreement(wavelet, shape, levels):
             maxabs = float(np.max(np.abs(x)))
             d = float((got.double() - ref.double()).abs().max())
             assert d <= 2 * TOL_F32 * maxabs, (scheme, d / maxabs)
+
+
+@pytest.mark.parametrize("wavelet,dtype,scheme", [
+    ("cdf97", torch.float32, "nonsep_reduced"), ("cdf97", torch.float32, "separable"),
+    ("cdf97", torch.float32, "nonsep"), ("legall53", torch.int32, "nonsep_reduced"),
+    ("cdf97", torch.bfloat16, "nonsep_reduced")])
+def test_programmatic_launch_changes_nothing(monkeypatch, wavelet, dtype, scheme):
+    """Launches with programmatic stream serialization start while the one
+    before them drains and wait in griddepcontrol.wait before their first
+    global access.  Chained transforms issued back to back on one stream (each
+    forward overwrites what the previous inverse read, each inverse reads what
+    the forward just wrote) give the same bits as serialized launches."""
+    h, w, levels = 2050, 3001, 6
+    x = make_input(wavelet, h, w, seed=99)
+    if dtype == torch.bfloat16:
+        x = x / float(np.max(np.abs(x)))
+    xt = torch.from_numpy(x).to(dtype)
+    res = {}
+    for pdl in ("0", "1"):
+        monkeypatch.setenv("DWT2D_PDL", pdl)
+        plan = D.Plan(h, w, levels, wavelet, scheme, dtype)
+        assert plan.info()[0] >= 3
+        ws = plan.workspace()
+        src = _dev16(xt)
+        c = D.empty_image(h, w, dtype)
+        r = D.empty_image(h, w, dtype)
+        for _ in range(4):
+            plan.forward(src, c, ws)
+            plan.inverse(c, r, ws)
+            plan.forward(r, c, ws)
+        torch.cuda.synchronize()
+        assert plan.status(ws) == 0
+        res[pdl] = (c.cpu(), r.cpu())
+    assert torch.equal(res["0"][0], res["1"][0])
+    assert torch.equal(res["0"][1], res["1"][1])
