@@ -24,6 +24,8 @@ struct Group {
 
 }  // namespace
 
+constexpr int kMaxHostBands = 64;  // row bands of the pipelined host-buffer entry points
+
 struct dwt2d_plan_s {
     int H, W, levels;
     dwt2d_wavelet wavelet;
@@ -55,7 +57,8 @@ struct dwt2d_plan_s {
     // host-buffer forward: copy streams and events (created on first use)
     bool host_ready;
     cudaStream_t host_in, host_out;
-    cudaEvent_t host_ev[2 * 8 + 3];
+    cudaEvent_t host_ev[2 * kMaxHostBands + 3];
+    int host_bands;  // row bands of the pipelined host-buffer entry points
 };
 
 // A batch: per-image plans, workspace regions and the launch list.
@@ -652,6 +655,7 @@ static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width
                              : sms * env_int("DWT2D_INV_WARPS_PER_SM_LARGE", 48);
     p->fwd_q1 = env_int("DWT2D_FWD_Q", 2) == 4 && !half ? 4 : 2;
     p->pdl = env_int("DWT2D_PDL", 1) != 0;
+    p->host_bands = std::min(std::max(env_int("DWT2D_HOST_BANDS", 8), 1), kMaxHostBands);
     p->inv_q1 = env_int("DWT2D_INV_Q", 2) == 4 && !half ? 4 : 2;
 
     // workspace: header | LL buffer A | LL buffer B | (multipass) X | Y
@@ -745,7 +749,6 @@ dwt2d_status dwt2d_inverse(dwt2d_plan_t p, const void* d_src, int64_t sp, void* 
                                 : run_fused(p, false, d_src, sp, d_dst, dp, d_ws, as_stream(stream));
 }
 
-constexpr int kHostBands = 8;
 
 static bool host_resources(dwt2d_plan_s* p) {
     if (p->host_ready) return true;
@@ -794,7 +797,11 @@ static dwt2d_status run_host_fwd_pipelined(dwt2d_plan_s* p, const void* h_src, i
     char* dout = reinterpret_cast<char*>(d_out);
     char* wsb = reinterpret_cast<char*>(d_ws);
     int* err = reinterpret_cast<int*>(wsb);
-    cudaEvent_t* ev = p->host_ev;  // [0] start, [1..8] bands in, [9..16] launches, [17] end, [18] out
+    const int B = p->host_bands;
+    cudaEvent_t* ev = p->host_ev;  // [0] start, then per band: arrived, launched; end, out
+    auto ev_in = [&](int c) { return ev[1 + c]; };
+    auto ev_run = [&](int c) { return ev[1 + kMaxHostBands + c]; };
+    cudaEvent_t ev_end = ev[1 + 2 * kMaxHostBands], ev_out = ev[2 + 2 * kMaxHostBands];
     auto copy2d = [](char* dst, int64_t dp, const char* src, int64_t sp, int64_t w, int64_t rows,
                      cudaMemcpyKind kind, cudaStream_t s) {
         if (rows <= 0 || w <= 0) return cudaSuccess;
@@ -805,12 +812,12 @@ static dwt2d_status run_host_fwd_pipelined(dwt2d_plan_s* p, const void* h_src, i
     if (cudaEventRecord(ev[0], st) != cudaSuccess || cudaStreamWaitEvent(p->host_in, ev[0], 0) ||
         cudaStreamWaitEvent(p->host_out, ev[0], 0))
         return DWT2D_ERR_CUDA;
-    const int rb = (p->H + kHostBands - 1) / kHostBands;
-    for (int c = 0; c < kHostBands; ++c) {
+    const int rb = (p->H + B - 1) / B;
+    for (int c = 0; c < B; ++c) {
         const int r0 = std::min(c * rb, p->H), r1 = std::min(r0 + rb, p->H);
         if (copy2d(din + r0 * dpitch, dpitch, hs + r0 * hsp, hsp, row, r1 - r0, cudaMemcpyHostToDevice,
                    p->host_in) != cudaSuccess ||
-            cudaEventRecord(ev[1 + c], p->host_in) != cudaSuccess)
+            cudaEventRecord(ev_in(c), p->host_in) != cudaSuccess)
             return DWT2D_ERR_CUDA;
     }
     const int elem_kind = elem_kind_of(p->dtype);
@@ -824,20 +831,20 @@ static dwt2d_status run_host_fwd_pipelined(dwt2d_plan_s* p, const void* h_src, i
     FusedArgs base = g0.a;
     base.seg_f = 1;
     int next = 0;  // first segment not launched yet
-    for (int c = 0; c < kHostBands && next < base.nsegs; ++c) {
+    for (int c = 0; c < B && next < base.nsegs; ++c) {
         const int avail = std::min((c + 1) * rb, p->H);
         int end = next;
-        while (end < base.nsegs && (c == kHostBands - 1 || seg_input_end(p, base, nl0, rho, end) <= avail))
+        while (end < base.nsegs && (c == B - 1 || seg_input_end(p, base, nl0, rho, end) <= avail))
             ++end;
         if (end == next) continue;
         FusedArgs a = base;
         a.seg_lo = next;
         a.nsegs = end - next;
         const int grid = (a.nstrips * a.nsegs + kFwdWarps - 1) / kFwdWarps;
-        if (cudaStreamWaitEvent(st, ev[1 + c], 0) != cudaSuccess ||
+        if (cudaStreamWaitEvent(st, ev_in(c), 0) != cudaSuccess ||
             launch_fwd_fused(elem_kind, sch, nl0, g0.q1, g0.m[0], a, grid, st) != cudaSuccess ||
-            cudaEventRecord(ev[9 + c], st) != cudaSuccess ||
-            cudaStreamWaitEvent(p->host_out, ev[9 + c], 0) != cudaSuccess)
+            cudaEventRecord(ev_run(c), st) != cudaSuccess ||
+            cudaStreamWaitEvent(p->host_out, ev_run(c), 0) != cudaSuccess)
             return DWT2D_ERR_CUDA;
         // the detail bands of levels 1..nl0 in these segments' rows are final
         for (int l = 0; l < nl0; ++l) {
@@ -861,7 +868,7 @@ static dwt2d_status run_host_fwd_pipelined(dwt2d_plan_s* p, const void* h_src, i
         next = end;
     }
     // every band has arrived before the call returns (the input buffer is free)
-    if (cudaStreamWaitEvent(st, ev[kHostBands], 0) != cudaSuccess) return DWT2D_ERR_CUDA;
+    if (cudaStreamWaitEvent(st, ev_in(B - 1), 0) != cudaSuccess) return DWT2D_ERR_CUDA;
     for (int k = 1; k < p->ngroups; ++k) {
         GroupLaunch gl;
         s = build_group(p, true, k, d_in, dpitch / es, d_out, dpitch / es, wsb, err, p->fwd_warps_target,
@@ -873,10 +880,10 @@ static dwt2d_status run_host_fwd_pipelined(dwt2d_plan_s* p, const void* h_src, i
     // the region of the later levels (and the last LL): rows [0, ne_r), columns [0, ne_c)
     const int hl = base.lv[nl0 - 1].h, wl = base.lv[nl0 - 1].w;
     const int ner = (hl + 1) >> 1, nec = (wl + 1) >> 1;
-    if (cudaEventRecord(ev[17], st) != cudaSuccess || cudaStreamWaitEvent(p->host_out, ev[17], 0) ||
+    if (cudaEventRecord(ev_end, st) != cudaSuccess || cudaStreamWaitEvent(p->host_out, ev_end, 0) ||
         copy2d(hd, hdp, dout, dpitch, (int64_t)nec * es, ner, cudaMemcpyDeviceToHost, p->host_out) !=
             cudaSuccess ||
-        cudaEventRecord(ev[18], p->host_out) != cudaSuccess || cudaStreamWaitEvent(st, ev[18], 0))
+        cudaEventRecord(ev_out, p->host_out) != cudaSuccess || cudaStreamWaitEvent(st, ev_out, 0))
         return DWT2D_ERR_CUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? DWT2D_OK : DWT2D_ERR_CUDA;
 }
@@ -896,7 +903,11 @@ static dwt2d_status run_host_inv_pipelined(dwt2d_plan_s* p, const void* h_src, i
     char* dout = reinterpret_cast<char*>(d_out);
     char* wsb = reinterpret_cast<char*>(d_ws);
     int* err = reinterpret_cast<int*>(wsb);
-    cudaEvent_t* ev = p->host_ev;  // [0] start, [1..8] bands in, [9..16] launches, [17] end
+    const int B = p->host_bands;
+    cudaEvent_t* ev = p->host_ev;  // [0] start, then per band: arrived, launched; end
+    auto ev_in = [&](int c) { return ev[1 + c]; };
+    auto ev_run = [&](int c) { return ev[1 + kMaxHostBands + c]; };
+    cudaEvent_t ev_end = ev[1 + 2 * kMaxHostBands];
     auto copy2d = [](char* dst, int64_t dp, const char* src, int64_t sp, int64_t w, int64_t rows,
                      cudaMemcpyKind kind, cudaStream_t s) {
         if (rows <= 0 || w <= 0) return cudaSuccess;
@@ -917,25 +928,25 @@ static dwt2d_status run_host_inv_pipelined(dwt2d_plan_s* p, const void* h_src, i
     // the finest group's detail bands by row bands of level-1 quadruple rows
     const int ne_r1 = (p->hs[0] + 1) / 2;
     const int unit = 1 << (n0 - 1);
-    const int rb = ((ne_r1 + kHostBands - 1) / kHostBands + unit - 1) / unit * unit;
-    for (int c = 0; c < kHostBands; ++c) {
+    const int rb = ((ne_r1 + B - 1) / B + unit - 1) / unit * unit;
+    for (int c = 0; c < B; ++c) {
         for (int l = 0; l < n0; ++l) {
             const int h = p->hs[l], w = p->ws[l];
             const int ne_r = (h + 1) >> 1, no_r = h >> 1, ne_c = (w + 1) >> 1;
             const int q0 = std::min((c * rb) >> l, ne_r);
-            const int q1 = c == kHostBands - 1 ? ne_r : std::min(((c + 1) * rb) >> l, ne_r);
+            const int q1 = c == B - 1 ? ne_r : std::min(((c + 1) * rb) >> l, ne_r);
             if (q1 <= q0) continue;
             if (in_rows(q0, q1, ne_c, w) != cudaSuccess) return DWT2D_ERR_CUDA;  // HL
             const int r1 = std::min(q1, no_r);
             if (r1 > q0 && in_rows(ne_r + q0, ne_r + r1, 0, w) != cudaSuccess) return DWT2D_ERR_CUDA;
         }
-        if (cudaEventRecord(ev[1 + c], p->host_in) != cudaSuccess) return DWT2D_ERR_CUDA;
+        if (cudaEventRecord(ev_in(c), p->host_in) != cudaSuccess) return DWT2D_ERR_CUDA;
     }
     const int elem_kind = elem_kind_of(p->dtype);
     const int sch = base_scheme(p->scheme);
     const int G = p->ngroups;
     // coarse groups: their input (the coarse region) went in first
-    if (G > 1 && cudaStreamWaitEvent(st, ev[1], 0) != cudaSuccess) return DWT2D_ERR_CUDA;
+    if (G > 1 && cudaStreamWaitEvent(st, ev_in(0), 0) != cudaSuccess) return DWT2D_ERR_CUDA;
     for (int k = 0; k + 1 < G; ++k) {
         GroupLaunch gl;
         dwt2d_status s = build_group(p, false, k, d_in, dpitch / es, d_out, dpitch / es, wsb, err,
@@ -957,7 +968,7 @@ static dwt2d_status run_host_inv_pipelined(dwt2d_plan_s* p, const void* h_src, i
     const int pro_slots = n0 == 2 ? lag : 0;
     const int ne_r2 = n0 == 2 ? (p->hs[1] + 1) / 2 : 0;
     auto ready = [&](int seg, int c) {  // rows segment `seg` reads are all in after band c
-        if (c == kHostBands - 1) return true;
+        if (c == B - 1) return true;
         const int A0 = seg * base.segq, A1 = std::min(A0 + base.segq, ne_r1);
         const int qstart = std::max(A0 - lag, 0) & ~3;
         const int nmain = (A1 + lag - qstart + 3) / 4;
@@ -971,7 +982,7 @@ static dwt2d_status run_host_inv_pipelined(dwt2d_plan_s* p, const void* h_src, i
         return true;
     };
     int next = 0;
-    for (int c = 0; c < kHostBands && next < base.nsegs; ++c) {
+    for (int c = 0; c < B && next < base.nsegs; ++c) {
         int end = next;
         while (end < base.nsegs && ready(end, c)) ++end;
         if (end == next) continue;
@@ -979,11 +990,11 @@ static dwt2d_status run_host_inv_pipelined(dwt2d_plan_s* p, const void* h_src, i
         a.seg_lo = next;
         a.nsegs = end - next;
         const int grid = (a.nstrips * a.nsegs + kInvTmaWarps - 1) / kInvTmaWarps;
-        if (cudaStreamWaitEvent(st, ev[1 + c], 0) != cudaSuccess ||
+        if (cudaStreamWaitEvent(st, ev_in(c), 0) != cudaSuccess ||
             launch_inv_tma(elem_kind, sch, gf.nl, gf.q1, gf.m[0], gf.m[1], gf.m[2], a, grid, st) !=
                 cudaSuccess ||
-            cudaEventRecord(ev[9 + c], st) != cudaSuccess ||
-            cudaStreamWaitEvent(p->host_out, ev[9 + c], 0) != cudaSuccess)
+            cudaEventRecord(ev_run(c), st) != cudaSuccess ||
+            cudaStreamWaitEvent(p->host_out, ev_run(c), 0) != cudaSuccess)
             return DWT2D_ERR_CUDA;
         const int y0 = std::min(2 * next * base.segq, p->H);
         const int y1 = std::min(2 * std::min(end * base.segq, ne_r1), p->H);
@@ -992,8 +1003,8 @@ static dwt2d_status run_host_inv_pipelined(dwt2d_plan_s* p, const void* h_src, i
             return DWT2D_ERR_CUDA;
         next = end;
     }
-    if (cudaStreamWaitEvent(st, ev[kHostBands], 0) != cudaSuccess ||
-        cudaEventRecord(ev[17], p->host_out) != cudaSuccess || cudaStreamWaitEvent(st, ev[17], 0))
+    if (cudaStreamWaitEvent(st, ev_in(B - 1), 0) != cudaSuccess ||
+        cudaEventRecord(ev_end, p->host_out) != cudaSuccess || cudaStreamWaitEvent(st, ev_end, 0))
         return DWT2D_ERR_CUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? DWT2D_OK : DWT2D_ERR_CUDA;
 }

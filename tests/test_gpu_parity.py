@@ -234,3 +234,30 @@ def test_programmatic_launch_changes_nothing(monkeypatch, wavelet, dtype, scheme
         res[pdl] = (c.cpu(), r.cpu())
     assert torch.equal(res["0"][0], res["1"][0])
     assert torch.equal(res["0"][1], res["1"][1])
+
+
+@pytest.mark.parametrize("bands", ["1", "5", "64"])
+@pytest.mark.parametrize("h,w,levels,wavelet,dtype", [
+    (1030, 2050, 5, "cdf97", torch.float32), (2051, 777, 3, "legall53", torch.int32)])
+def test_host_pipelined_band_counts(monkeypatch, bands, h, w, levels, wavelet, dtype):
+    """Any number of row bands (one, a ragged count, more bands than row
+    segments) gives the device entry points' results bit for bit."""
+    monkeypatch.setenv("DWT2D_HOST_BANDS", bands)
+    x = make_input(wavelet, h, w, seed=h + 3 * w)
+    xt = torch.from_numpy(x).to(dtype)
+    plan = D.Plan(h, w, levels, wavelet, "nonsep_reduced", dtype)
+    ws = plan.workspace()
+    hs = xt.pin_memory()
+    hd = torch.full_like(hs, 3).pin_memory()
+    din = D.empty_image(h, w, dtype)
+    dout = D.empty_image(h, w, dtype)
+    plan.forward_host(hs, hd, din, dout, ws)
+    ref = plan.forward(_dev16(xt))
+    torch.cuda.synchronize()
+    assert torch.equal(hd, ref.cpu())
+    back = torch.full_like(hs, 9).pin_memory()
+    plan.inverse_host(hd, back, din, dout, ws)
+    ref_back = plan.inverse(_dev16(hd))
+    torch.cuda.synchronize()
+    assert torch.equal(back, ref_back.cpu())
+    assert plan.status(ws) == 0
