@@ -46,6 +46,7 @@ struct dwt2d_plan_s {
     int inv_q1;  // the same for the inverse
     int min_segq;
     int pdl;  // device entry points: launches with programmatic stream serialization
+    int inv_seg_f;  // inverse segment interleave (0: as many groups as waves)
     // workspace layout (bytes from the start of the workspace)
     size_t off_a, off_b, off_x, off_y;
     size_t size_a, size_b;  // bytes of the two LL buffers
@@ -374,6 +375,8 @@ dwt2d_status build_group(const dwt2d_plan_s* p, bool fwd, int k, const void* src
                 out->grid = grid_b;
             }
         }
+        // the inverse measured fastest with its segments top to bottom
+        if (p->inv_seg_f > 0) a.seg_f = p->inv_seg_f;
         out->path = 1;
         out->q1 = q1;
     } else {
@@ -643,18 +646,21 @@ static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width
     p->inv_warps_target = sms * (tuning && tuning->warps_per_sm > 0 ? tuning->warps_per_sm
                                                                     : env_int("DWT2D_INV_WARPS_PER_SM", 12));
     p->min_segq = tuning && tuning->min_segment > 0 ? tuning->min_segment : env_int("DWT2D_MIN_SEGQ", 2);
-    // measured at 8192^2: the first forward launch is fastest at about 44
-    // warps per SM (2.75 waves of 16), the small later ones at one wave
+    // measured at 8192^2: the first forward launch is fastest at 48 warps
+    // per SM (3 waves of 16) for CDF 9/7 and at 44 for LeGall 5/3 (its
+    // shorter halo), the small later ones at one wave
     p->fwd_warps_large = tuning && tuning->warps_per_sm > 0
                              ? 0
-                             : sms * env_int("DWT2D_FWD_WARPS_PER_SM_LARGE", 44);
+                             : sms * env_int("DWT2D_FWD_WARPS_PER_SM_LARGE",
+                                             wavelet == DWT2D_CDF97 ? 48 : 44);
     p->large_segq = env_int("DWT2D_LARGE_SEGQ", 16);
-    // the finest inverse launch: about 48 warps per SM (3 waves of 16)
+    // the finest inverse launch: 64 warps per SM (4 waves of 16)
     p->inv_warps_large = tuning && tuning->warps_per_sm > 0
                              ? 0
-                             : sms * env_int("DWT2D_INV_WARPS_PER_SM_LARGE", 48);
+                             : sms * env_int("DWT2D_INV_WARPS_PER_SM_LARGE", 64);
     p->fwd_q1 = env_int("DWT2D_FWD_Q", 2) == 4 && !half ? 4 : 2;
     p->pdl = env_int("DWT2D_PDL", 1) != 0;
+    p->inv_seg_f = env_int("DWT2D_INV_SEG_INTERLEAVE", 1);
     p->host_bands = std::min(std::max(env_int("DWT2D_HOST_BANDS", 8), 1), kMaxHostBands);
     p->inv_q1 = env_int("DWT2D_INV_Q", 2) == 4 && !half ? 4 : 2;
 
