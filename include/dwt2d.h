@@ -125,6 +125,14 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
  *   stream          a cudaStream_t (NULL = legacy default stream).
  *   Asynchronous on stream.  Errors: DWT2D_ERR_INVALID, DWT2D_ERR_ALIGN,
  *   DWT2D_ERR_CUDA.
+ *   The streaming kernels are launched with programmatic stream
+ *   serialization (environment DWT2D_PDL=0 at plan creation turns it off): a
+ *   launch may become resident while the kernel before it on `stream` (the
+ *   call's previous launch, or the caller's own kernel) drains, and every
+ *   thread waits for that kernel's completion and memory before its first
+ *   global access.  Stream order is unchanged for the caller.  An event
+ *   recorded between two launches (dwt2d_plan_set_launch_events) suspends
+ *   the overlap of those two.
  */
 dwt2d_status dwt2d_forward(dwt2d_plan_t plan, const void* d_src, int64_t src_pitch_bytes,
                            void* d_dst, int64_t dst_pitch_bytes, void* d_workspace,
@@ -149,7 +157,8 @@ dwt2d_status dwt2d_inverse(dwt2d_plan_t plan, const void* d_src, int64_t src_pit
  *   bands on an internal stream, the first level group runs on `stream` band
  *   by band as its input rows arrive, and the finished detail bands come back
  *   on a second internal stream while later bands still go in (the plan owns
- *   the two streams; a plan's _host calls must not overlap each other).  The
+ *   the two streams; a plan's _host calls must not overlap each other; the
+ *   band count is DWT2D_HOST_BANDS at plan creation, default 8).  The
  *   inverse does the same the other way round: the coarse levels' top-left
  *   region goes in first, the finest level group runs by row bands as their
  *   detail bands arrive, and finished image rows come back meanwhile.
