@@ -360,7 +360,8 @@ def main():
                    "launches_per_step": launches, "fused_levels_per_launch": fused,
                    "l2": "inputs and outputs (256 MiB each) larger than L2; no flush",
                    "parallelism": f"replicas x{ws}"},
-        "gpu_launches": launches * K,
+        # pass 1 (step time) and pass 2 (launch 0 bracketed by events)
+        "gpu_launches": 2 * launches * K,
         "roofline": roofline,
         "clocks": clocks,
     }
@@ -390,7 +391,12 @@ def main():
     out["e2e"] = {"value": round(ws * H * W / e2e_s / 1e9, 3), "unit": UNIT,
                   "h2d_bytes_per_step": 4 * H * W, "d2h_bytes_per_step": 4 * H * W,
                   "steps": n_e2e, "api": "dwt2d_forward_host (pinned host buffers)"}
-    out["gpu_launches"] += launches * (n_e2e + 2)
+    # a host-buffer call at this size: one launch of the first level group per
+    # row band (every band completes some of its row segments) plus one per
+    # later group
+    bands = int(os.environ.get("DWT2D_HOST_BANDS", "8"))
+    out["e2e"]["gpu_launches_per_step"] = bands + launches - 1
+    out["gpu_launches"] += n_e2e * (bands + launches - 1)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
