@@ -391,12 +391,13 @@ def main():
     out["e2e"] = {"value": round(ws * H * W / e2e_s / 1e9, 3), "unit": UNIT,
                   "h2d_bytes_per_step": 4 * H * W, "d2h_bytes_per_step": 4 * H * W,
                   "steps": n_e2e, "api": "dwt2d_forward_host (pinned host buffers)"}
-    # a host-buffer call at this size: one launch of the first level group per
-    # row band (every band completes some of its row segments) plus one per
-    # later group
+    # a pipelined host-buffer call (1024 rows or more): one launch of the first
+    # level group per row band (at 8192^2 every band completes some of its row
+    # segments) plus one per later group; below that the plain launches
     bands = int(os.environ.get("DWT2D_HOST_BANDS", "8"))
-    out["e2e"]["gpu_launches_per_step"] = bands + launches - 1
-    out["gpu_launches"] += n_e2e * (bands + launches - 1)
+    per_call = bands + launches - 1 if H >= 1024 else launches
+    out["e2e"]["gpu_launches_per_step"] = per_call
+    out["gpu_launches"] += n_e2e * per_call
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
