@@ -262,14 +262,15 @@ class Server:
         return t.result
 
     def stats(self) -> dict:
-        lat = sorted(self.latencies)
+        with self._lock:
+            lat = sorted(self.latencies)
+            c = dict(self.counts)
 
         def q(p):
             if not lat:
                 return None
             return lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))]
 
-        c = self.counts
         return {"completed": c[DONE], "failed": c[FAILED], "cancelled": c[CANCELLED],
                 "rejected": c[REJECTED], "p50_s": q(0.50), "p99_s": q(0.99),
                 "max_s": lat[-1] if lat else None, "batches": self.batches,
@@ -277,10 +278,11 @@ class Server:
 
     def reset_stats(self):
         """Forget the counts and latencies so far (e.g. after a warm-up)."""
-        self.counts = {k: 0 for k in self.counts}
-        self.latencies = []
-        self.batches = 0
-        self.peak = self.in_use
+        with self._lock:
+            self.counts = {k: 0 for k in self.counts}
+            self.latencies = []
+            self.batches = 0
+            self.peak = self.in_use
 
     def close(self):
         self._loaders.shutdown(wait=True)
@@ -332,9 +334,10 @@ class Server:
         if state != DONE:
             t.result = None
             t._src = None
-        self.counts[state] = self.counts.get(state, 0) + 1
-        if state == DONE:
-            self.latencies.append(t.t_done - t.t_submit)
+        with self._lock:  # loader threads finish failed loads concurrently
+            self.counts[state] = self.counts.get(state, 0) + 1
+            if state == DONE:
+                self.latencies.append(t.t_done - t.t_submit)
         t._event.set()
 
     def admit_and_launch(self):

@@ -227,3 +227,23 @@ def test_result_drives_the_loop_and_reports_failures():
     with pytest.raises(TimeoutError):
         srv.result(slow, timeout=0.05)
     assert torch.all(srv.result(slow, timeout=5) == 0.0)
+
+
+def test_counts_exact_with_concurrent_loader_failures():
+    """Loader threads finish failed loads while the polling thread finishes
+    completed batches: every request is counted exactly once."""
+    def boom():
+        time.sleep(0.001)
+        raise IOError("gone")
+
+    srv = S.Server(budget_bytes=1 << 30, executor=FakeExecutor(), loader_threads=8)
+    bad = [srv.submit(S.Request(8, 8, 1, loader=boom)) for _ in range(150)]
+    good = [srv.submit(req(fill=float(i))) for i in range(150)]
+    assert srv.run_until_idle(10)
+    st = srv.stats()
+    assert st["failed"] == 150 and st["completed"] == 150
+    assert all(t.state == S.FAILED for t in bad) and all(t.state == S.DONE for t in good)
+    srv.reset_stats()
+    st = srv.stats()
+    assert st["completed"] == 0 and st["p99_s"] is None
+    srv.close()
