@@ -7,8 +7,9 @@ waves), and the smallest segment.  The best setting depends on the mix of
 image sizes and level counts, so the tuner times a small set of candidates on
 the batch itself (CUDA events, on the caller's buffers: the outputs are
 overwritten) and keeps the fastest.  Results are cached in a JSON file keyed
-by a signature of the batch: per job its storage type, wavelet, direction,
-level count and the power-of-two class of each side.
+by a signature of the batch (per job its storage type, wavelet, direction,
+level count and the power-of-two class of each side) and by the device and
+library build it was measured on.
 """
 from __future__ import annotations
 
@@ -67,10 +68,12 @@ def save_cache(path: str, data: dict) -> None:
 
 
 def pick(sig: str, measure: Callable[[dict], float], candidates=None, cache_path: Optional[str] = None,
-         scheme: str = "nonsep_reduced") -> dict:
+         scheme: str = "nonsep_reduced", context: str = "") -> dict:
     """The fastest candidate for signature `sig` (cached).  measure(tuning)
-    returns milliseconds, or None when the candidate does not apply."""
-    key = f"{scheme}:{sig}"
+    returns milliseconds, or None when the candidate does not apply.
+    `context` (the device and library build) is part of the cache key, so a
+    tuning measured elsewhere is not reused."""
+    key = f"{scheme}:{context}:{sig}" if context else f"{scheme}:{sig}"
     cache = load_cache(cache_path) if cache_path else {}
     if key in cache and "tuning" in cache[key]:
         return dict(cache[key]["tuning"])
@@ -121,4 +124,8 @@ def tune(jobs, scheme: str = "nonsep_reduced", cache_path: Optional[str] = None,
         e1.synchronize()
         return e0.elapsed_time(e1) / iters
 
-    return pick(signature(descs), measure, candidates, cache_path, scheme)
+    dev = jobs[0][0].device
+    props = torch.cuda.get_device_properties(dev)
+    st_lib = os.stat(D.LIB_PATH)
+    context = f"{props.name}/{props.multi_processor_count}sm/lib{st_lib.st_size}.{st_lib.st_mtime_ns}"
+    return pick(signature(descs), measure, candidates, cache_path, scheme, context)

@@ -52,3 +52,21 @@ def test_corrupt_cache_is_ignored(tmp_path):
     best = A.pick("s", lambda t: float(t["warps_per_sm"]), cache_path=str(path))
     assert best["warps_per_sm"] == 12
     assert "nonsep_reduced:s" in json.loads(path.read_text())
+
+
+def test_context_separates_cache_entries(tmp_path):
+    """A tuning measured on another device or library build is not reused."""
+    path = str(tmp_path / "tune.json")
+    calls = []
+
+    def measure(t):
+        calls.append(t)
+        return float(t["warps_per_sm"])
+
+    A.pick("sig", measure, cache_path=path, context="GPU-A/152sm/lib1")
+    n = len(calls)
+    A.pick("sig", measure, cache_path=path, context="GPU-A/152sm/lib1")
+    assert len(calls) == n  # cached
+    A.pick("sig", measure, cache_path=path, context="GPU-B/132sm/lib1")
+    assert len(calls) == 2 * n  # measured again
+    assert len(json.load(open(path))) == 2
