@@ -115,6 +115,48 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
                         dwt2d_dtype dtype, size_t* workspace_bytes);
 
 /*
+ * dwt2d_plan_options -- how a plan cuts its work into launches.  These knobs
+ *   change the launch decomposition, never the coefficients: every setting
+ *   gives the same result bit for bit.  Every field 0 = the library default
+ *   (measured fastest on GB300 at 8192 x 8192, 5 levels); switches take
+ *   1 = on, -1 = off.  The library reads no environment variables.
+ */
+typedef struct {
+    int32_t fuse_first;            /* levels fused in the first launch, 1-3 (default 2) */
+    int32_t fuse_max;              /* at most per later launch, 1-3 (default 2; 3 runs 4 quadruple
+                                      columns per lane; 16-bit storage caps both at 2) */
+    int32_t fwd_warps_per_sm;      /* warps a forward launch is cut into, per SM (default 16) */
+    int32_t inv_warps_per_sm;      /* the same for the inverse (default 12) */
+    int32_t fwd_warps_per_sm_large;/* forward launches whose row segments stay at least
+                                      large_segment rows long at this many warps per SM take it
+                                      (default 48 for CDF 9/7, 44 for LeGall 5/3; -1: never) */
+    int32_t inv_warps_per_sm_large;/* the same for the inverse (default 64; -1: never) */
+    int32_t large_segment;         /* that threshold, quadruple rows of the launch's last level
+                                      (default 16) */
+    int32_t min_segment;           /* shortest row segment of a warp (default 2) */
+    int32_t fwd_seg_interleave;    /* forward segment order: taken in this many interleaved groups
+                                      (default: the launch's waves of resident warps; 1: top to
+                                      bottom) */
+    int32_t inv_seg_interleave;    /* the same for the inverse (default 1; -1: the launch's waves) */
+    int32_t fwd_cols_per_lane;     /* quadruple columns per lane, 2 or 4 (default 2; 16-bit: 2) */
+    int32_t inv_cols_per_lane;     /* the same for the inverse (default 2) */
+    int32_t programmatic_launch;   /* device entry points launch with programmatic stream
+                                      serialization (default on) */
+    int32_t host_bands;            /* row bands of the *_host entry points, 1-64 (default 8) */
+    int32_t host_pipeline;         /* *_host entry points overlap copies and transform (default on) */
+} dwt2d_plan_options;
+
+/*
+ * dwt2d_plan_ex -- dwt2d_plan with launch options (NULL = all defaults, which
+ *   is what dwt2d_plan does).  Errors as dwt2d_plan, plus DWT2D_ERR_INVALID
+ *   for an option out of its range.
+ */
+dwt2d_status dwt2d_plan_ex(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,
+                           dwt2d_wavelet wavelet, dwt2d_scheme scheme, dwt2d_boundary boundary,
+                           dwt2d_dtype dtype, const dwt2d_plan_options* options,
+                           size_t* workspace_bytes);
+
+/*
  * dwt2d_forward -- image -> Mallat-layout coefficients (Sec. 2 and Sec. 3).
  *   d_src           height x width elements of the plan's dtype, row pitch
  *                   src_pitch_bytes.  Not modified.
@@ -218,9 +260,10 @@ dwt2d_status dwt2d_plan_set_launch_events(dwt2d_plan_t plan, void** events, int3
  *   still passes the image and the coefficient buffer, exactly as for
  *   dwt2d_forward, and gets the same coefficients.
  *
- *   - The first call on each device looks up that device's address of the
- *     array (cudaGetSymbolAddress) with the device current; make that first
- *     call before any stream capture.
+ *   - Every call looks up the current device's address of the array
+ *     (cudaGetSymbolAddress) with the caller's device current.  The first
+ *     call on a device may load the library's device code there; make that
+ *     first call before any stream capture.
  *   - A plan whose workspace_bytes exceeds DWT2D_NOALLOC_SCRATCH_BYTES is
  *     rejected with DWT2D_ERR_INVALID before any GPU work (for example an
  *     8192 x 8192 float image with 5 levels fits, 16384 x 16384 with 6 levels
@@ -232,11 +275,21 @@ dwt2d_status dwt2d_plan_set_launch_events(dwt2d_plan_t plan, void** events, int3
  *     stream) race on the array and corrupt each other's results: serialise
  *     them, for example on one stream.
  *   - Nothing here calls cudaMalloc, cudaFree or an allocating library
- *     routine.  Errors: as dwt2d_forward.
+ *     routine.  The arguments are checked as dwt2d_forward checks them, and
+ *     a call that is refused puts nothing on the stream.  Kernel errors
+ *     (a bounded wait that gave up) land in the array's status word, which
+ *     the caller has no address for: read them with dwt2d_noalloc_status.
+ *
+ * dwt2d_noalloc_status -- dwt2d_workspace_status for the array above:
+ *   synchronizes stream, returns DWT2D_OK or the error the kernels of the
+ *   calls so far recorded (DWT2D_ERR_TIMEOUT, or DWT2D_ERR_BOUNDS in a
+ *   bounds-checked build), and resets the status word to zero.  The next
+ *   dwt2d_forward_noalloc clears it too, so read it before that call.
  */
 #define DWT2D_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 dwt2d_status dwt2d_forward_noalloc(dwt2d_plan_t plan, const void* d_src, int64_t src_pitch_bytes,
                                    void* d_dst, int64_t dst_pitch_bytes, float scale, void* stream);
+dwt2d_status dwt2d_noalloc_status(void* stream);
 
 /*
  * Batched transforms -- many images of different sizes, level counts,
@@ -266,11 +319,14 @@ typedef struct {
 /* Tuning knobs (0 = library default): levels fused in the first launch of an
  * image (1 or 2; default 2), at most per later launch (1 or 2; default 2),
  * warps per SM that the rows of one launch are cut into (default 48; the
- * batched kernels keep 12 warps per SM resident, so 48 is four waves), and the
+ * batched kernels keep 12 warps per SM resident, so 48 is four waves), the
  * smallest row segment of a warp (quadruple rows of the last fused level;
- * default 2).  Every warp of a launch streams the same number of rows. */
+ * default 2), and whether the batch's launches use programmatic stream
+ * serialization (1 on, -1 or 0 off: measured neutral to 1 % slower for
+ * batches).  Every warp of a launch streams the same number of rows. */
 typedef struct {
     int32_t fuse_first, fuse_max, warps_per_sm, min_segment;
+    int32_t programmatic_launch;
 } dwt2d_tuning;
 
 /*

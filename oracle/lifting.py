@@ -14,7 +14,7 @@ Paper: Barina et al., arXiv 1705.08266.
   c3 = x[2r+1, 2c+1], consistent with T_P^H updating components 1 and 3 from
   components 0 and 2.
 
-Readings where the paper is silent (each one is listed in the design doc):
+Readings where the paper is silent:
 
 * Lifting filters: predict P = p (1 + z) reads the even sample at i and i+1,
   update U = u (1 + z^-1) reads the odd sample at i-1 and i.  CDF 9/7 uses

@@ -122,6 +122,10 @@ def tune(jobs, scheme: str = "nonsep_reduced", cache_path: Optional[str] = None,
             b.launch(ws, stream=st)
         e1.record(st)
         e1.synchronize()
+        # a candidate whose kernels recorded an error (a wait that gave up,
+        # a caught store) is not a valid timing: reject it
+        if b.status(ws, stream=st) != 0:
+            return None
         return e0.elapsed_time(e1) / iters
 
     dev = jobs[0][0].device

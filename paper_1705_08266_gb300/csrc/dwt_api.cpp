@@ -46,7 +46,9 @@ struct dwt2d_plan_s {
     int inv_q1;  // the same for the inverse
     int min_segq;
     int pdl;  // device entry points: launches with programmatic stream serialization
+    int fwd_seg_f;  // forward segment interleave (0: as many groups as waves)
     int inv_seg_f;  // inverse segment interleave (0: as many groups as waves)
+    int host_pipeline;  // *_host entry points overlap copies and transform
     // workspace layout (bytes from the start of the workspace)
     size_t off_a, off_b, off_x, off_y;
     size_t size_a, size_b;  // bytes of the two LL buffers
@@ -131,11 +133,6 @@ int base_scheme(dwt2d_scheme s) {
     }
 }
 
-int env_int(const char* name, int dflt) {
-    const char* v = getenv(name);
-    if (!v || !*v) return dflt;
-    return atoi(v);
-}
 
 void level_scale(int h, int w, bool inverse, float s[4]) {
     const double K = 1.230174104914001;
@@ -248,7 +245,7 @@ void decompose(const dwt2d_plan_s* p, int w_first, int rows, int nl, int rho, in
     // resident warps (16 per SM), so vertically adjacent segments run one
     // after the other and share their halo rows through L2 (measured 1-2 %)
     const int resident = p->sm_count * 16;
-    a->seg_f = env_int("DWT2D_SEG_INTERLEAVE", (items + resident / 2) / resident);
+    a->seg_f = p->fwd_seg_f > 0 ? p->fwd_seg_f : (items + resident / 2) / resident;
     if (a->seg_f < 1) a->seg_f = 1;
 }
 
@@ -574,22 +571,55 @@ extern "C" {
 
 static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,
                                 dwt2d_wavelet wavelet, dwt2d_scheme scheme, dwt2d_boundary boundary,
-                                dwt2d_dtype dtype, size_t* workspace_bytes, const dwt2d_tuning* tuning);
+                                dwt2d_dtype dtype, size_t* workspace_bytes, const dwt2d_tuning* tuning,
+                                const dwt2d_plan_options* opts);
 
 dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,
                         dwt2d_wavelet wavelet, dwt2d_scheme scheme, dwt2d_boundary boundary,
                         dwt2d_dtype dtype, size_t* workspace_bytes) {
     return plan_create(out, height, width, levels, wavelet, scheme, boundary, dtype, workspace_bytes,
-                       nullptr);
+                       nullptr, nullptr);
+}
+
+dwt2d_status dwt2d_plan_ex(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,
+                           dwt2d_wavelet wavelet, dwt2d_scheme scheme, dwt2d_boundary boundary,
+                           dwt2d_dtype dtype, const dwt2d_plan_options* options,
+                           size_t* workspace_bytes) {
+    return plan_create(out, height, width, levels, wavelet, scheme, boundary, dtype, workspace_bytes,
+                       nullptr, options);
 }
 
 }  // extern "C"
 
+// An option field: its value, or dflt when it is 0.
+static int opt(int v, int dflt) { return v != 0 ? v : dflt; }
+
+// Options in range (0 = default everywhere).
+static bool options_ok(const dwt2d_plan_options& o) {
+    auto in = [](int v, int lo, int hi) { return v == 0 || (v >= lo && v <= hi); };
+    auto sw = [](int v) { return v == 0 || v == 1 || v == -1; };
+    return in(o.fuse_first, 1, kMaxFused) && in(o.fuse_max, 1, kMaxFused) &&
+           in(o.fwd_warps_per_sm, 1, 1 << 16) && in(o.inv_warps_per_sm, 1, 1 << 16) &&
+           (o.fwd_warps_per_sm_large == -1 || in(o.fwd_warps_per_sm_large, 1, 1 << 16)) &&
+           (o.inv_warps_per_sm_large == -1 || in(o.inv_warps_per_sm_large, 1, 1 << 16)) &&
+           in(o.large_segment, 1, 1 << 16) && in(o.min_segment, 1, 1 << 16) &&
+           in(o.fwd_seg_interleave, 1, 1 << 16) &&
+           (o.inv_seg_interleave == -1 || in(o.inv_seg_interleave, 1, 1 << 16)) &&
+           (o.fwd_cols_per_lane == 0 || o.fwd_cols_per_lane == 2 || o.fwd_cols_per_lane == 4) &&
+           (o.inv_cols_per_lane == 0 || o.inv_cols_per_lane == 2 || o.inv_cols_per_lane == 4) &&
+           sw(o.programmatic_launch) && in(o.host_bands, 1, kMaxHostBands) && sw(o.host_pipeline);
+}
+
 static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,
                                 dwt2d_wavelet wavelet, dwt2d_scheme scheme, dwt2d_boundary boundary,
-                                dwt2d_dtype dtype, size_t* workspace_bytes, const dwt2d_tuning* tuning) {
+                                dwt2d_dtype dtype, size_t* workspace_bytes, const dwt2d_tuning* tuning,
+                                const dwt2d_plan_options* opts) {
     if (!out || !workspace_bytes) return DWT2D_ERR_INVALID;
     *out = nullptr;
+    dwt2d_plan_options o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (!options_ok(o)) return DWT2D_ERR_INVALID;
     if (height < 1 || width < 1 || height > 65536 || width > 65536) return DWT2D_ERR_INVALID;
     if (levels < 1 || levels > 16) return DWT2D_ERR_INVALID;
     if (boundary != DWT2D_SYMMETRIC_WHOLE) return DWT2D_ERR_UNSUPPORTED;
@@ -619,12 +649,12 @@ static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width
     // level groups: the first launch fuses DWT2D_FUSE_FIRST levels (default 2),
     // later launches up to DWT2D_FUSE (default 2; 3 needs 4 columns per lane,
     // which measured slower) each
-    int maxf = tuning && tuning->fuse_max > 0 ? tuning->fuse_max : env_int("DWT2D_FUSE", 2);
+    int maxf = tuning && tuning->fuse_max > 0 ? tuning->fuse_max : opt(o.fuse_max, 2);
     if (maxf < 1) maxf = 1;
     if (maxf > kMaxFused) maxf = kMaxFused;
     if (half && maxf > 2) maxf = 2;  // 16-bit storage runs 2 columns per lane: up to 2 levels
     int first = tuning && tuning->fuse_first > 0 ? tuning->fuse_first
-                                                 : env_int("DWT2D_FUSE_FIRST", maxf < 2 ? maxf : 2);
+                                                 : opt(o.fuse_first, maxf < 2 ? maxf : 2);
     if (first < 1) first = 1;
     if (first > maxf) first = maxf;
     p->ngroups = 0;
@@ -642,27 +672,26 @@ static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width
     cudaGetLastError();
     p->sm_count = sms;
     p->fwd_warps_target = sms * (tuning && tuning->warps_per_sm > 0 ? tuning->warps_per_sm
-                                                                    : env_int("DWT2D_FWD_WARPS_PER_SM", 16));
+                                                                    : opt(o.fwd_warps_per_sm, 16));
     p->inv_warps_target = sms * (tuning && tuning->warps_per_sm > 0 ? tuning->warps_per_sm
-                                                                    : env_int("DWT2D_INV_WARPS_PER_SM", 12));
-    p->min_segq = tuning && tuning->min_segment > 0 ? tuning->min_segment : env_int("DWT2D_MIN_SEGQ", 2);
+                                                                    : opt(o.inv_warps_per_sm, 12));
+    p->min_segq = tuning && tuning->min_segment > 0 ? tuning->min_segment : opt(o.min_segment, 2);
     // measured at 8192^2: the first forward launch is fastest at 48 warps
     // per SM (3 waves of 16) for CDF 9/7 and at 44 for LeGall 5/3 (its
     // shorter halo), the small later ones at one wave
-    p->fwd_warps_large = tuning && tuning->warps_per_sm > 0
-                             ? 0
-                             : sms * env_int("DWT2D_FWD_WARPS_PER_SM_LARGE",
-                                             wavelet == DWT2D_CDF97 ? 48 : 44);
-    p->large_segq = env_int("DWT2D_LARGE_SEGQ", 16);
+    const int fwl = opt(o.fwd_warps_per_sm_large, wavelet == DWT2D_CDF97 ? 48 : 44);
+    p->fwd_warps_large = (tuning && tuning->warps_per_sm > 0) || fwl < 0 ? 0 : sms * fwl;
+    p->large_segq = opt(o.large_segment, 16);
     // the finest inverse launch: 64 warps per SM (4 waves of 16)
-    p->inv_warps_large = tuning && tuning->warps_per_sm > 0
-                             ? 0
-                             : sms * env_int("DWT2D_INV_WARPS_PER_SM_LARGE", 64);
-    p->fwd_q1 = env_int("DWT2D_FWD_Q", 2) == 4 && !half ? 4 : 2;
-    p->pdl = env_int("DWT2D_PDL", 1) != 0;
-    p->inv_seg_f = env_int("DWT2D_INV_SEG_INTERLEAVE", 1);
-    p->host_bands = std::min(std::max(env_int("DWT2D_HOST_BANDS", 8), 1), kMaxHostBands);
-    p->inv_q1 = env_int("DWT2D_INV_Q", 2) == 4 && !half ? 4 : 2;
+    const int iwl = opt(o.inv_warps_per_sm_large, 64);
+    p->inv_warps_large = (tuning && tuning->warps_per_sm > 0) || iwl < 0 ? 0 : sms * iwl;
+    p->fwd_q1 = o.fwd_cols_per_lane == 4 && !half ? 4 : 2;
+    p->pdl = opt(o.programmatic_launch, 1) > 0;
+    p->fwd_seg_f = o.fwd_seg_interleave;
+    p->inv_seg_f = o.inv_seg_interleave < 0 ? 0 : opt(o.inv_seg_interleave, 1);
+    p->host_bands = opt(o.host_bands, 8);
+    p->host_pipeline = opt(o.host_pipeline, 1) > 0;
+    p->inv_q1 = o.inv_cols_per_lane == 4 && !half ? 4 : 2;
 
     // workspace: header | LL buffer A | LL buffer B | (multipass) X | Y
     size_t off = kHeader;
@@ -734,12 +763,22 @@ static bool scale_ok(const dwt2d_plan_s* p, float scale) {
     return scale > 0.0f && scale < 3.0e38f;
 }
 
+}  // extern "C"
+
+dwt2d_status dwt::check_transform_args(dwt2d_plan_t p, const void* src, int64_t sp, const void* dst,
+                                       int64_t dp, const void* ws, float scale) {
+    dwt2d_status s = check_buffers(p, src, sp, dst, dp, ws);
+    if (s == DWT2D_OK && !scale_ok(p, scale)) s = DWT2D_ERR_INVALID;
+    if (s == DWT2D_OK && src == dst) s = DWT2D_ERR_INVALID;
+    return s;
+}
+
+extern "C" {
+
 dwt2d_status dwt2d_forward(dwt2d_plan_t p, const void* d_src, int64_t sp, void* d_dst, int64_t dp,
                            void* d_ws, float scale, void* stream) {
-    dwt2d_status s = check_buffers(p, d_src, sp, d_dst, dp, d_ws);
-    if (s == DWT2D_OK && !scale_ok(p, scale)) s = DWT2D_ERR_INVALID;
+    const dwt2d_status s = dwt::check_transform_args(p, d_src, sp, d_dst, dp, d_ws, scale);
     if (s != DWT2D_OK) return s;
-    if (d_src == d_dst) return DWT2D_ERR_INVALID;
     if (convolution(p->scheme)) return run_conv_fwd(p, d_src, sp, d_dst, dp, d_ws, as_stream(stream));
     return multipass(p->scheme) ? run_multipass(p, true, d_src, sp, d_dst, dp, d_ws, as_stream(stream))
                                 : run_fused(p, true, d_src, sp, d_dst, dp, d_ws, as_stream(stream));
@@ -747,10 +786,8 @@ dwt2d_status dwt2d_forward(dwt2d_plan_t p, const void* d_src, int64_t sp, void* 
 
 dwt2d_status dwt2d_inverse(dwt2d_plan_t p, const void* d_src, int64_t sp, void* d_dst, int64_t dp,
                            void* d_ws, float scale, void* stream) {
-    dwt2d_status s = check_buffers(p, d_src, sp, d_dst, dp, d_ws);
-    if (s == DWT2D_OK && !scale_ok(p, scale)) s = DWT2D_ERR_INVALID;
+    const dwt2d_status s = dwt::check_transform_args(p, d_src, sp, d_dst, dp, d_ws, scale);
     if (s != DWT2D_OK) return s;
-    if (d_src == d_dst) return DWT2D_ERR_INVALID;
     return multipass(p->scheme) ? run_multipass(p, false, d_src, sp, d_dst, dp, d_ws, as_stream(stream))
                                 : run_fused(p, false, d_src, sp, d_dst, dp, d_ws, as_stream(stream));
 }
@@ -1023,11 +1060,10 @@ static dwt2d_status run_host(dwt2d_plan_t p, bool fwd, const void* h_src, int64_
     if (hsp < row || hdp < row) return DWT2D_ERR_INVALID;
     cudaStream_t st = as_stream(stream);
     if (fwd && p->H >= 1024 && !multipass(p->scheme) && !convolution(p->scheme) &&
-        env_int("DWT2D_HOST_PIPELINE", 1) != 0 && check_buffers(p, d_in, dpitch, d_out, dpitch, d_ws) ==
-                                                      DWT2D_OK &&
+        p->host_pipeline && check_buffers(p, d_in, dpitch, d_out, dpitch, d_ws) == DWT2D_OK &&
         p->groups[0].n <= 2 && scale_ok(p, scale) && host_resources(p))
         return run_host_fwd_pipelined(p, h_src, hsp, h_dst, hdp, d_in, d_out, dpitch, d_ws, st);
-    if (!fwd && p->H >= 1024 && !multipass(p->scheme) && env_int("DWT2D_HOST_PIPELINE", 1) != 0 &&
+    if (!fwd && p->H >= 1024 && !multipass(p->scheme) && p->host_pipeline &&
         check_buffers(p, d_in, dpitch, d_out, dpitch, d_ws) == DWT2D_OK && p->groups[0].n <= 2 &&
         p->inv_q1 == 2 && scale_ok(p, scale) && host_resources(p))
         return run_host_inv_pipelined(p, h_src, hsp, h_dst, hdp, d_in, d_out, dpitch, d_ws, st);
@@ -1137,7 +1173,7 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
     dwt2d_batch_s* b = new (std::nothrow) dwt2d_batch_s();
     if (!b) return DWT2D_ERR_NOMEM;
     b->scheme = scheme;
-    b->pdl = env_int("DWT2D_BATCH_PDL", 0) != 0;  // measured neutral to 1 % slower for batches
+    b->pdl = tun.programmatic_launch > 0;  // default off: measured neutral to 1 % slower for batches
     b->items.assign(items, items + n);
     size_t off = kHeader;
     b->table_off = off;
@@ -1146,7 +1182,7 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
         dwt2d_plan_t p = nullptr;
         size_t wsb = 0;
         dwt2d_status s = plan_create(&p, it.height, it.width, it.levels, it.wavelet, scheme,
-                                     DWT2D_SYMMETRIC_WHOLE, it.dtype, &wsb, &tun);
+                                     DWT2D_SYMMETRIC_WHOLE, it.dtype, &wsb, &tun, nullptr);
         if (s == DWT2D_OK && (it.inverse != 0 && it.inverse != 1)) s = DWT2D_ERR_INVALID;
         if (s == DWT2D_OK) s = check_buffers(p, it.d_src, it.src_pitch_bytes, it.d_dst,
                                              it.dst_pitch_bytes, it.d_src);

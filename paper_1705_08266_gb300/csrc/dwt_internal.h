@@ -146,4 +146,10 @@ enum PassKind { P_TH = 0, P_TV, P_SH, P_SV, P_T, P_S, P_TR, P_SR };
 // Workspace bytes a plan needs (0 for a null plan).
 size_t plan_workspace_bytes(dwt2d_plan_t p);
 
+// The argument checks of dwt2d_forward / dwt2d_inverse (buffers, alignment,
+// pitches, 16-bit scale, src != dst), without any GPU work.
+dwt2d_status check_transform_args(dwt2d_plan_t p, const void* src, int64_t src_pitch_bytes,
+                                  const void* dst, int64_t dst_pitch_bytes, const void* ws,
+                                  float scale);
+
 }  // namespace dwt

@@ -50,7 +50,28 @@ class BatchItem(ctypes.Structure):
 class Tuning(ctypes.Structure):
     """dwt2d_tuning (0 = library default)."""
     _fields_ = [("fuse_first", ctypes.c_int32), ("fuse_max", ctypes.c_int32),
-                ("warps_per_sm", ctypes.c_int32), ("min_segment", ctypes.c_int32)]
+                ("warps_per_sm", ctypes.c_int32), ("min_segment", ctypes.c_int32),
+                ("programmatic_launch", ctypes.c_int32)]
+
+
+class PlanOptions(ctypes.Structure):
+    """dwt2d_plan_options (0 = library default; switches 1 on, -1 off)."""
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "fuse_first", "fuse_max", "fwd_warps_per_sm", "inv_warps_per_sm", "fwd_warps_per_sm_large",
+        "inv_warps_per_sm_large", "large_segment", "min_segment", "fwd_seg_interleave",
+        "inv_seg_interleave", "fwd_cols_per_lane", "inv_cols_per_lane", "programmatic_launch",
+        "host_bands", "host_pipeline")]
+
+
+def plan_options(**kw) -> PlanOptions:
+    """A dwt2d_plan_options with the named fields set (unknown names raise)."""
+    o = PlanOptions()
+    names = {f[0] for f in PlanOptions._fields_}
+    for k, v in kw.items():
+        if k not in names:
+            raise KeyError(f"unknown plan option {k!r}")
+        setattr(o, k, int(v))
+    return o
 
 
 class DwtError(RuntimeError):
@@ -70,6 +91,9 @@ def lib() -> ctypes.CDLL:
     vp, i32, i64, f32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
     L.dwt2d_plan.argtypes = [ctypes.POINTER(vp), i32, i32, i32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                              ctypes.c_int, ctypes.POINTER(sz)]
+    L.dwt2d_plan_ex.argtypes = [ctypes.POINTER(vp), i32, i32, i32, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_int, ctypes.POINTER(PlanOptions), ctypes.POINTER(sz)]
+    L.dwt2d_noalloc_status.argtypes = [vp]
     for name in ("dwt2d_forward", "dwt2d_inverse"):
         getattr(L, name).argtypes = [vp, vp, i64, vp, i64, vp, f32, vp]
     for name in ("dwt2d_forward_host", "dwt2d_inverse_host"):
@@ -90,7 +114,8 @@ def lib() -> ctypes.CDLL:
     L.dwt2d_batch_destroy.restype = None
     L.dwt2d_status_string.argtypes = [ctypes.c_int]
     L.dwt2d_status_string.restype = ctypes.c_char_p
-    for name in ("dwt2d_plan", "dwt2d_forward", "dwt2d_inverse", "dwt2d_forward_host",
+    for name in ("dwt2d_plan", "dwt2d_plan_ex", "dwt2d_noalloc_status", "dwt2d_forward",
+                 "dwt2d_inverse", "dwt2d_forward_host",
                  "dwt2d_inverse_host", "dwt2d_workspace_init", "dwt2d_workspace_status",
                  "dwt2d_plan_info", "dwt2d_batch_create", "dwt2d_batch_upload",
                  "dwt2d_batch_launch", "dwt2d_batch_info"):
@@ -143,7 +168,9 @@ class Plan:
     """A transform description (dwt2d_plan) plus convenience wrappers."""
 
     def __init__(self, height: int, width: int, levels: int, wavelet: str = "cdf97",
-                 scheme: str = "nonsep_reduced", dtype: Optional[torch.dtype] = None):
+                 scheme: str = "nonsep_reduced", dtype: Optional[torch.dtype] = None,
+                 options: Optional[dict] = None):
+        """options: dwt2d_plan_options fields by name (launch decomposition only)."""
         L = lib()
         if dtype is None:
             dtype = torch.int32 if wavelet == "legall53" else torch.float32
@@ -151,8 +178,10 @@ class Plan:
         self.wavelet, self.scheme, self.dtype = wavelet, scheme, dtype
         self._h = ctypes.c_void_p()
         ws = ctypes.c_size_t()
-        _check(L.dwt2d_plan(ctypes.byref(self._h), height, width, levels, WAVELETS[wavelet],
-                            SCHEMES[scheme], 0, DTYPES[dtype], ctypes.byref(ws)), "dwt2d_plan")
+        opts = ctypes.byref(plan_options(**options)) if options else None
+        _check(L.dwt2d_plan_ex(ctypes.byref(self._h), height, width, levels, WAVELETS[wavelet],
+                               SCHEMES[scheme], 0, DTYPES[dtype], opts, ctypes.byref(ws)),
+               "dwt2d_plan_ex")
         self.workspace_bytes = ws.value
 
     def __del__(self):
@@ -191,7 +220,8 @@ class Plan:
         src = as_pitched(src)
         if dst is None:
             dst = empty_image(self.height, self.width, self.dtype, src.device)
-        if workspace is None:
+        own_ws = workspace is None
+        if own_ws:
             workspace = self.workspace(src.device, stream)
         es = src.element_size()
         st = getattr(lib(), name)(self._h, ctypes.c_void_p(src.data_ptr()), src.stride(0) * es,
@@ -199,6 +229,10 @@ class Plan:
                                   ctypes.c_void_p(workspace.data_ptr()), float(scale),
                                   _stream_ptr(stream))
         _check(st, name)
+        if own_ws:
+            # nobody else can read the status word of a workspace made here:
+            # read it now (synchronizes the stream) so kernel errors surface
+            _check(self.status(workspace, stream), name + " (kernel status)")
         return dst
 
     def forward(self, src: torch.Tensor, dst: Optional[torch.Tensor] = None,
@@ -255,7 +289,8 @@ class Batch:
         tun = None
         if tuning is not None:
             tun = ctypes.byref(Tuning(*[int(tuning.get(k, 0)) for k in
-                                        ("fuse_first", "fuse_max", "warps_per_sm", "min_segment")]))
+                                        ("fuse_first", "fuse_max", "warps_per_sm", "min_segment",
+                                         "programmatic_launch")]))
         self._h = ctypes.c_void_p()
         ws = ctypes.c_size_t()
         _check(L.dwt2d_batch_create(ctypes.byref(self._h), arr, len(self.jobs), SCHEMES[scheme], tun,

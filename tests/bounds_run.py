@@ -30,9 +30,7 @@ def main():
                     for fuse in ("1", "2", "3"):
                         if fuse == "3" and dt == torch.float16:
                             continue
-                        import os
-                        os.environ["DWT2D_FUSE"] = fuse
-                        plan = D.Plan(h, w, lv, wavelet, scheme, dt)
+                        plan = D.Plan(h, w, lv, wavelet, scheme, dt, options=dict(fuse_max=int(fuse)))
                         ws = plan.workspace()
                         c = plan.forward(xd, workspace=ws)
                         plan.inverse(c, workspace=ws)

@@ -150,3 +150,36 @@ def test_batch_validation(L, case, status):
     assert st == status
     if st == 0:
         L.dwt2d_batch_destroy(b)
+
+
+@pytest.mark.parametrize("opts,status", [
+    ({}, 0), ({"fuse_first": 3, "fuse_max": 3}, 0), ({"fwd_cols_per_lane": 4}, 0),
+    ({"programmatic_launch": -1, "host_pipeline": -1, "inv_seg_interleave": -1}, 0),
+    ({"fwd_warps_per_sm_large": -1, "host_bands": 64}, 0),
+    ({"fuse_first": 4}, -1), ({"fuse_max": -2}, -1), ({"fwd_cols_per_lane": 3}, -1),
+    ({"programmatic_launch": 2}, -1), ({"host_bands": 65}, -1), ({"min_segment": -1}, -1),
+])
+def test_plan_options_validation(L, opts, status):
+    """dwt2d_plan_ex checks every launch option's range; defaults are all zeros."""
+    p = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    o = D.plan_options(**opts)
+    st = L.dwt2d_plan_ex(ctypes.byref(p), 512, 512, 5, 0, 2, 0, 0, ctypes.byref(o), ctypes.byref(ws))
+    assert st == status
+    if st == 0:
+        L.dwt2d_plan_destroy(p)
+
+
+def test_plan_options_change_the_launch_decomposition_only(L):
+    """fuse_max = 1 gives one launch per level; the workspace grows with the LL it keeps."""
+    for fm, groups in ((1, [1, 1, 1, 1, 1]), (2, [2, 2, 1]), (3, [2, 3])):
+        p = ctypes.c_void_p()
+        ws = ctypes.c_size_t()
+        o = D.plan_options(fuse_max=fm)
+        assert L.dwt2d_plan_ex(ctypes.byref(p), 1024, 1024, 5, 0, 2, 0, 0, ctypes.byref(o),
+                               ctypes.byref(ws)) == 0
+        n, ng = ctypes.c_int32(), ctypes.c_int32()
+        fused = (ctypes.c_int32 * 16)()
+        assert L.dwt2d_plan_info(p, ctypes.byref(n), fused, ctypes.byref(ng)) == 0
+        assert [fused[i] for i in range(ng.value)] == groups
+        L.dwt2d_plan_destroy(p)

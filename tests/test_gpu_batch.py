@@ -223,15 +223,14 @@ def test_autotune_picks_a_candidate_and_caches(tmp_path):
     _assert_same_as_single(jobs, "nonsep_reduced", "autotuned")
 
 
-def test_programmatic_batch_launch_changes_nothing(monkeypatch):
+def test_programmatic_batch_launch_changes_nothing():
     """Batched launches with programmatic stream serialization (off by
     default), eager and replayed from a CUDA graph: the same bits as the
     serialized launches."""
     out = {}
     for pdl in ("0", "1"):
-        monkeypatch.setenv("DWT2D_BATCH_PDL", pdl)
         jobs, _ = _jobs(MIXED, 555)
-        batch = D.Batch(jobs)
+        batch = D.Batch(jobs, tuning=dict(programmatic_launch=int(pdl)))
         ws = batch.workspace()
         side = torch.cuda.Stream()
         batch.upload(ws, stream=side)

@@ -5,7 +5,8 @@ Every scheme: forward coefficients sampled at band corners, band edges and
 random positions, each recomputed by the oracle from its dependency window
 (oracle.lifting.sample_coefficient); and the GPU round trip.  The headline
 scheme (non-separable reduced, CDF 9/7) and the 5/3 scheme are also compared
-element by element against the full FP64 oracle.
+element by element against the full FP64 oracle, forward and inverse (the
+inverse of the oracle's own coefficients against the oracle's inverse).
 """
 import numpy as np
 import pytest
@@ -87,3 +88,24 @@ def test_fullsize_elementwise(images, wavelet, scheme):
         maxabs = float(np.max(np.abs(x)))
         for lvl, e in per_level_errors(c, ref, LEVELS).items():
             assert e <= TOL_F32 * maxabs, (lvl, e)
+
+
+@pytest.mark.parametrize("wavelet,scheme", [("cdf97", "nonsep_reduced"), ("legall53", "nonsep")])
+def test_fullsize_inverse_elementwise(images, wavelet, scheme):
+    """GPU inverse of the oracle's coefficients == oracle inverse (Eq. 2 undone, coarse to fine)."""
+    x = images[wavelet]
+    coeffs = L.forward(x, LEVELS, wavelet).astype(x.dtype)  # what the GPU is given
+    ref = L.inverse(coeffs, LEVELS, wavelet)
+    plan = D.Plan(H, W, LEVELS, wavelet, scheme)
+    ws = plan.workspace()
+    cd = device_image(coeffs)
+    y = plan.inverse(cd, workspace=ws)
+    torch.cuda.synchronize()
+    assert plan.status(ws) == 0
+    yh = y.cpu().numpy()
+    if wavelet == "legall53":
+        assert np.array_equal(yh.astype(np.int64), ref)
+    else:
+        # the inverse's one output is held to the forward's per-level bound
+        maxabs = float(np.max(np.abs(x)))
+        assert float(np.max(np.abs(yh.astype(np.float64) - ref))) <= TOL_F32 * maxabs

@@ -40,9 +40,9 @@ def _lib():
     D.lib()
 
 
-def _fwd_inv(x, levels, wavelet, scheme):
+def _fwd_inv(x, levels, wavelet, scheme, options=None):
     h, w = x.shape
-    plan = D.Plan(h, w, levels, wavelet, scheme)
+    plan = D.Plan(h, w, levels, wavelet, scheme, options=options)
     ws = plan.workspace()
     xd = device_image(x)
     c = plan.forward(xd, workspace=ws)
@@ -67,16 +67,13 @@ def test_parity_all_schemes(wavelet, shape, levels):
 
 @pytest.mark.parametrize("fuse", ["1", "2", "3"])
 @pytest.mark.parametrize("wavelet", ["cdf97", "legall53"])
-def test_parity_many_segments_and_fusion(monkeypatch, fuse, wavelet):
+def test_parity_many_segments_and_fusion(fuse, wavelet):
     """Tiny row segments (many warps per strip) and every fusion depth."""
-    monkeypatch.setenv("DWT2D_FUSE", fuse)
-    monkeypatch.setenv("DWT2D_MIN_SEGQ", "1")
-    monkeypatch.setenv("DWT2D_FWD_WARPS_PER_SM", "4000")
-    monkeypatch.setenv("DWT2D_INV_WARPS_PER_SM", "4000")
+    opts = dict(fuse_max=int(fuse), min_segment=1, fwd_warps_per_sm=4000, inv_warps_per_sm=4000)
     for shape, levels in [((200, 777), 3), ((97, 515), 5), ((450, 250), 4)]:
         x = make_input(wavelet, *shape, seed=11 + shape[1])
         for scheme in ("separable", "nonsep", "nonsep_reduced"):
-            c, y, ref = _fwd_inv(x, levels, wavelet, scheme)
+            c, y, ref = _fwd_inv(x, levels, wavelet, scheme, opts)
             tag = f"fuse={fuse} {wavelet} {scheme} {shape} L{levels}"
             assert_forward_matches(c, x, levels, wavelet, tag)
             assert_inverse_matches(y, ref.astype(x.dtype), levels, wavelet, x, tag)
@@ -205,7 +202,7 @@ def test_cross_scheme_agreement(wavelet, shape, levels):
     ("cdf97", torch.float32, "nonsep_reduced"), ("cdf97", torch.float32, "separable"),
     ("cdf97", torch.float32, "nonsep"), ("legall53", torch.int32, "nonsep_reduced"),
     ("cdf97", torch.bfloat16, "nonsep_reduced")])
-def test_programmatic_launch_changes_nothing(monkeypatch, wavelet, dtype, scheme):
+def test_programmatic_launch_changes_nothing(wavelet, dtype, scheme):
     """Launches with programmatic stream serialization start while the one
     before them drains and wait in griddepcontrol.wait before their first
     global access.  Chained transforms issued back to back on one stream (each
@@ -218,8 +215,8 @@ def test_programmatic_launch_changes_nothing(monkeypatch, wavelet, dtype, scheme
     xt = torch.from_numpy(x).to(dtype)
     res = {}
     for pdl in ("0", "1"):
-        monkeypatch.setenv("DWT2D_PDL", pdl)
-        plan = D.Plan(h, w, levels, wavelet, scheme, dtype)
+        plan = D.Plan(h, w, levels, wavelet, scheme, dtype,
+                      options=dict(programmatic_launch=1 if pdl == "1" else -1))
         assert plan.info()[0] >= 3
         ws = plan.workspace()
         src = _dev16(xt)
@@ -239,13 +236,12 @@ def test_programmatic_launch_changes_nothing(monkeypatch, wavelet, dtype, scheme
 @pytest.mark.parametrize("bands", ["1", "5", "64"])
 @pytest.mark.parametrize("h,w,levels,wavelet,dtype", [
     (1030, 2050, 5, "cdf97", torch.float32), (2051, 777, 3, "legall53", torch.int32)])
-def test_host_pipelined_band_counts(monkeypatch, bands, h, w, levels, wavelet, dtype):
+def test_host_pipelined_band_counts(bands, h, w, levels, wavelet, dtype):
     """Any number of row bands (one, a ragged count, more bands than row
     segments) gives the device entry points' results bit for bit."""
-    monkeypatch.setenv("DWT2D_HOST_BANDS", bands)
     x = make_input(wavelet, h, w, seed=h + 3 * w)
     xt = torch.from_numpy(x).to(dtype)
-    plan = D.Plan(h, w, levels, wavelet, "nonsep_reduced", dtype)
+    plan = D.Plan(h, w, levels, wavelet, "nonsep_reduced", dtype, options=dict(host_bands=int(bands)))
     ws = plan.workspace()
     hs = xt.pin_memory()
     hd = torch.full_like(hs, 3).pin_memory()

@@ -6,6 +6,8 @@ measures the transform (and the 16-bit rounding of its outputs and of the LL
 handed between launches), not the input quantisation.  Error per band and
 level <= 2e-3 * max|x| (FP16) and <= 1.6e-2 * max|x| (BF16).
 """
+import json
+
 import numpy as np
 import pytest
 import torch
@@ -97,10 +99,30 @@ def test_16bit_full_size_sampled(dtype):
                 [(0, 0, he, we)] if lvl == levels else []):
             pos += [(r0, c0), (r1 - 1, c1 - 1)]
             pos += [(int(rng.integers(r0, r1)), int(rng.integers(c0, c1))) for _ in range(6)]
+    worst = {}
     for r, cc in pos:
         ref = L.sample_coefficient(xdq32, levels, "cdf97", r, cc)
         got = float(ch[r, cc].to(torch.float64)) * scale
-        assert abs(got - ref) <= TOL[dtype] * maxabs, (r, cc, got, ref)
+        key = _band_of(r, cc, sizes, levels)
+        worst[key] = max(worst.get(key, 0.0), abs(got - ref) / maxabs)
+    # the achieved error per band and level, as a fraction of max|x| (printed
+    # for the record; pytest -s shows it)
+    print("precision_report", json.dumps({"dtype": str(dtype).replace("torch.", ""),
+                                          "image": [h, w], "levels": levels, "samples": len(pos),
+                                          "max_err_over_maxabs": {f"L{k[0]} {k[1]}": round(v, 7)
+                                                                  for k, v in sorted(worst.items())}}))
+    for k, v in worst.items():
+        assert v <= TOL[dtype], (k, v)
+
+
+def _band_of(r, c, sizes, levels):
+    """(level, band) of Mallat position (r, c)."""
+    for lvl, (hl, wl) in enumerate(sizes, start=1):
+        he, we = (hl + 1) // 2, (wl + 1) // 2
+        if r < hl and c < wl and (r >= he or c >= we or lvl == levels):
+            band = ("H" if c >= we else "L") + ("H" if r >= he else "L")
+            return lvl, band
+    raise ValueError((r, c))
 
 
 def test_16bit_rejects_bad_scale_and_multipass():

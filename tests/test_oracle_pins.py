@@ -288,6 +288,67 @@ def test_int53_close_to_linear():
     assert d.max() > 0.2  # the floors do act
 
 
+# --- the reversible 5/3 rounding rule (floor toward -inf, update offset +2) ---
+# The paper prints no rounding rule for its CDF 5/3; the reading is the usual
+# reversible 5/3 (floor of half the predict sum, floor of a quarter of the
+# update sum plus 2).  These pins fix both halves of that rule: a hand-worked
+# example (tests/golden/legall53_worked.json) and the exact rounding residuals
+# of each integer step against the linear step it rounds.
+
+def _worked():
+    with open(os.path.join(GOLDEN, "legall53_worked.json")) as f:
+        return json.load(f)
+
+
+def _worked_example_holds():
+    g = _worked()
+    x = np.array([g["one_d"]["x"]], dtype=np.int64)
+    ok = L.forward(x, 1, "legall53")[0].tolist() == g["one_d"]["mallat"]
+    ok = ok and L.forward(x.T.copy(), 1, "legall53")[:, 0].tolist() == g["one_d"]["mallat"]
+    y = np.array(g["two_d"]["x"], dtype=np.int64)
+    return ok and L.forward(y, 1, "legall53").tolist() == g["two_d"]["mallat"]
+
+
+def test_int53_worked_example():
+    """The oracle reproduces the hand-worked 1-D (row and column) and 2-D examples, and inverts them."""
+    assert _worked_example_holds()
+    g = _worked()
+    back = L.inverse(np.array(g["two_d"]["mallat"], dtype=np.int64), 1, "legall53")
+    assert back.tolist() == g["two_d"]["x"]
+
+
+def _step_residuals(axis):
+    """Sets of (integer step - linear step) over a signed random image, predict and update apart.
+
+    The predict residual is s/2 - floor(s/2) for the even-neighbour sum s, the
+    update residual floor((v + 2)/4) - v/4 for the odd-neighbour sum v; both
+    are taken on the same input, so each set isolates one rounding.
+    """
+    rng = np.random.default_rng(5)
+    x = rng.integers(-4096, 4097, size=(37, 41)).astype(np.int64)
+    a = x.copy()
+    L.predict_int53(a, axis)
+    b = x.astype(np.float64)
+    L.predict(b, -0.5, axis)
+    pred = set((a - b).ravel().tolist())
+    c = a.copy()
+    L.update_int53(c, axis)
+    d = a.astype(np.float64)
+    L.update(d, 0.25, axis)
+    upd = set((c - d).ravel().tolist())
+    return pred, upd
+
+
+@pytest.mark.parametrize("axis", [-1, -2])
+def test_int53_rounding_residuals(axis):
+    """floor((e_i + e_i+1)/2) differs from the linear half-sum by 0 or -1/2 (so d by 0 or +1/2),
+    floor((d_i-1 + d_i + 2)/4) from the linear quarter-sum by exactly {-1/4, 0, 1/4, 1/2};
+    every value occurs (signed inputs, every residue)."""
+    pred, upd = _step_residuals(axis)
+    assert pred == {0.0, 0.5}
+    assert upd == {-0.25, 0.0, 0.25, 0.5}
+
+
 # --- planted mistakes: the pins catch a perturbed oracle ----------------------
 
 @pytest.mark.parametrize("name", ["ALPHA", "BETA", "GAMMA", "DELTA", "K97"])
@@ -328,3 +389,37 @@ def test_sample_coefficient_matches_full_transform(wavelet):
     pos += [(int(rng.integers(h)), int(rng.integers(w))) for _ in range(40)]
     for r, c in pos:
         assert L.sample_coefficient(x, levels, wavelet, r, c) == pytest.approx(full[r, c], abs=1e-9), (r, c)
+
+
+# the two plausible misreadings of the rounding rule, planted in the oracle
+def _predict_int53_trunc(a, axis, sign=1):
+    if a.shape[axis] < 2:
+        return
+    even, odd = L._polyphase(a, axis)
+    no = odd.shape[-1]
+    s = even[..., :no] + L._even_next(even, no)
+    odd -= sign * np.trunc(s / 2).astype(a.dtype)  # rounds toward zero, not -inf
+
+
+def _update_int53_plus1(a, axis, sign=1):
+    if a.shape[axis] < 2:
+        return
+    even, odd = L._polyphase(a, axis)
+    prev, cur = L._odd_prev_cur(odd, even.shape[-1])
+    even += sign * np.floor_divide(prev + cur + 1, 4)  # offset +1 instead of +2
+
+
+@pytest.mark.parametrize("mutant", ["predict_truncates", "update_offset_1"])
+def test_int53_rounding_mistakes_are_caught(monkeypatch, mutant):
+    """Plant each misreading of the 5/3 rounding rule: the worked example and the residual sets fail."""
+    if mutant == "predict_truncates":
+        monkeypatch.setattr(L, "predict_int53", _predict_int53_trunc)
+    else:
+        monkeypatch.setattr(L, "update_int53", _update_int53_plus1)
+    assert not _worked_example_holds()
+    for axis in (-1, -2):
+        pred, upd = _step_residuals(axis)
+        assert pred != {0.0, 0.5} or upd != {-0.25, 0.0, 0.25, 0.5}
+    # a consistent misreading still inverts exactly: round trips alone cannot see it
+    x = synth.uniform_int(9, 7, seed=3) - 2048
+    assert np.array_equal(L.inverse(L.forward(x, 2, "legall53"), 2, "legall53"), x)
