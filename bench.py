@@ -568,9 +568,10 @@ def precision_variants(D, synth, dev, stream):
             # reference: the FP32-storage transform of the dequantised 16-bit image
             plan32 = D.Plan(n, n, levels, "cdf97", "nonsep_reduced", torch.float32)
             xd = D.empty_image(n, n, torch.float32, dev)
-            xd.copy_(x.to(torch.float32) * scale)
-            r32 = plan32.forward(xd, stream=stream)
-            plan.forward(x, c, wsb, scale=sc, stream=stream)
+            with torch.cuda.stream(stream):  # every step of the comparison on the one stream
+                xd.copy_(x.to(torch.float32) * scale)
+                r32 = plan32.forward(xd, stream=stream)
+                plan.forward(x, c, wsb, scale=sc, stream=stream)
             torch.cuda.synchronize()
             maxabs = float(xd.abs().max())
             errs = {}
