@@ -322,6 +322,7 @@ def main():
     plan = D.Plan(H, W, LEVELS, "cdf97", HEADLINE_SCHEME)
     wsb = plan.workspace(dev)
     launches, fused = plan.info()
+    shapes = plan.launch_info()  # (levels fused, columns per lane, warps) per launch
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
 
@@ -382,8 +383,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
                 "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": f"fwd_fused_kernel<float, nonsep_reduced, {fused[0]} levels, 2 columns/lane> "
-                          f"(launch {dom} of {launches})",
+                "kernel": f"fwd_fused_kernel<float, nonsep_reduced, {shapes[0][0]} levels, "
+                          f"{shapes[0][1]} columns/lane> (launch {dom} of {launches}, {shapes[0][2]} warps)",
                 "kernel_ms": round(launch_ms[dom], 5),
                 "kernel_timing": "CUDA events around launch 0 of each step, second pass of K steps",
                 "alg_bytes_per_launch": alg_bytes_dom,
@@ -402,6 +403,7 @@ def main():
         "config": {"workload": WORKLOAD,
                    "image": [H, W], "levels": LEVELS, "wavelet": "cdf97", "scheme": HEADLINE_SCHEME,
                    "launches_per_step": launches, "fused_levels_per_launch": fused,
+                   "launch_shapes": [{"levels": f, "cols_per_lane": q, "warps": w} for f, q, w in shapes],
                    "l2": "inputs and outputs (256 MiB each) larger than L2; no flush",
                    "parallelism": f"replicas x{ws}"},
         # pass 1 (step time) and pass 2 (launch 0 bracketed by events)

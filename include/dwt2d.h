@@ -116,8 +116,11 @@ dwt2d_status dwt2d_plan(dwt2d_plan_t* out, int32_t height, int32_t width, int32_
 
 /*
  * dwt2d_plan_options -- how a plan cuts its work into launches.  These knobs
- *   change the launch decomposition, never the coefficients: every setting
- *   gives the same result bit for bit.  Every field 0 = the library default
+ *   change the launch decomposition, not the arithmetic: every setting gives
+ *   the same result bit for bit, except that with 16-bit storage the LL
+ *   handed from one launch to the next is stored (rounded) in 16 bits, so
+ *   fuse_first / fuse_max move those roundings (the result stays within the
+ *   16-bit tolerance).  Every field 0 = the library default
  *   (measured fastest on GB300 at 8192 x 8192, 5 levels); switches take
  *   1 = on, -1 = off.  The library reads no environment variables.
  */
@@ -129,7 +132,8 @@ typedef struct {
     int32_t inv_warps_per_sm;      /* the same for the inverse (default 12) */
     int32_t fwd_warps_per_sm_large;/* forward launches whose row segments stay at least
                                       large_segment rows long at this many warps per SM take it
-                                      (default 48 for CDF 9/7, 44 for LeGall 5/3; -1: never) */
+                                      (default 48 for CDF 9/7, 44 for LeGall 5/3 at 2 columns per
+                                      lane, 24 at 4; -1: never) */
     int32_t inv_warps_per_sm_large;/* the same for the inverse (default 64; -1: never) */
     int32_t large_segment;         /* that threshold, quadruple rows of the launch's last level
                                       (default 16) */
@@ -138,12 +142,19 @@ typedef struct {
                                       (default: the launch's waves of resident warps; 1: top to
                                       bottom) */
     int32_t inv_seg_interleave;    /* the same for the inverse (default 1; -1: the launch's waves) */
-    int32_t fwd_cols_per_lane;     /* quadruple columns per lane, 2 or 4 (default 2; 16-bit: 2) */
+    int32_t fwd_cols_per_lane;     /* quadruple columns per lane, 2 or 4 (default: 4 for a float
+                                      launch of at most 2 fused levels whose rows give long
+                                      segments at 24 warps per SM, else 2) */
     int32_t inv_cols_per_lane;     /* the same for the inverse (default 2) */
     int32_t programmatic_launch;   /* device entry points launch with programmatic stream
                                       serialization (default on) */
     int32_t host_bands;            /* row bands of the *_host entry points, 1-64 (default 8) */
     int32_t host_pipeline;         /* *_host entry points overlap copies and transform (default on) */
+    int32_t fwd_short_tail;        /* in a large launch, the rows one wave of warps takes last are
+                                      cut into segments this many times shorter, 2-64, so that
+                                      the launch drains quickly (default 3 at 2 columns per lane,
+                                      4 at 4; -1: off) */
+    int32_t inv_short_tail;        /* the same for the inverse (default 4) */
 } dwt2d_plan_options;
 
 /*
@@ -233,6 +244,16 @@ dwt2d_status dwt2d_workspace_status(void* d_workspace, void* stream);
  */
 dwt2d_status dwt2d_plan_info(dwt2d_plan_t plan, int32_t* launches_per_call, int32_t* fused,
                              int32_t* n_groups);
+
+/*
+ * dwt2d_plan_launch_info -- the shape of launch i (in launch order) of a
+ *   forward (inverse = 0) or inverse (inverse = 1) call: levels fused,
+ *   quadruple columns per lane and warps.  Any output may be NULL.  Streaming
+ *   schemes only (DWT2D_ERR_UNSUPPORTED for the multipass schemes and the
+ *   convolution forward); needs no GPU.
+ */
+dwt2d_status dwt2d_plan_launch_info(dwt2d_plan_t plan, int32_t inverse, int32_t i, int32_t* fused,
+                                    int32_t* cols_per_lane, int32_t* warps);
 
 /*
  * dwt2d_plan_set_launch_events -- profiling hook.  With events != NULL, every

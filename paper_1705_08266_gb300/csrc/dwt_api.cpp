@@ -42,10 +42,12 @@ struct dwt2d_plan_s {
     // strips' unequal costs); smaller launches keep fwd_warps_target
     int fwd_warps_large, large_segq;
     int inv_warps_large;  // the same rule for inverse launches
-    int fwd_q1;  // quadruple columns per lane of the forward kernel (2 or 4)
+    int fwd_q1;  // quadruple columns per lane of the forward kernel (2 or 4; 0: automatic)
+    int fwd_warps_large4, fwd_short4;  // the large-launch rule at 4 columns per lane
     int inv_q1;  // the same for the inverse
     int min_segq;
     int pdl;  // device entry points: launches with programmatic stream serialization
+    int fwd_short, inv_short;  // short last-wave segments: divisor (0: off)
     int fwd_seg_f;  // forward segment interleave (0: as many groups as waves)
     int inv_seg_f;  // inverse segment interleave (0: as many groups as waves)
     int host_pipeline;  // *_host entry points overlap copies and transform
@@ -137,8 +139,11 @@ int base_scheme(dwt2d_scheme s) {
 void level_scale(int h, int w, bool inverse, float s[4]) {
     const double K = 1.230174104914001;
     const double kh = w > 1 ? K : 1.0, kv = h > 1 ? K : 1.0;
+    // each factor computed directly (not as a reciprocal of the other
+    // direction's), the way the kernels' border-free code rounds its constants
     const double f[4] = {1.0 / (kh * kv), kh / kv, kv / kh, kh * kv};
-    for (int k = 0; k < 4; ++k) s[k] = (float)(inverse ? 1.0 / f[k] : f[k]);
+    const double g[4] = {kh * kv, kv / kh, kh / kv, 1.0 / (kh * kv)};
+    for (int k = 0; k < 4; ++k) s[k] = (float)(inverse ? g[k] : f[k]);
 }
 
 // Lanes whose every column at the deepest fused level is valid, for a warp of
@@ -214,10 +219,20 @@ dwt2d_status check_buffers(const dwt2d_plan_s* p, const void* src, int64_t sp, c
     return DWT2D_OK;
 }
 
+// Warps of a streaming kernel resident per SM (their register budgets).
+int resident_per_sm(bool fwd, int nl, int q1, int scheme) {
+    if (fwd) return q1 <= 2 ? 16 : (nl <= 2 ? 12 : 8);
+    return q1 <= 2 ? (scheme == SCH_NONSEP ? 12 : 16) : 8;
+}
+
 // Warp work decomposition of one streaming launch.
 // Rows per warp: enough segments for target_warps warps, or segq_fixed (> 0).
+// With short_div > 1 the rows at the bottom that one wave of resident warps
+// (resident per SM) takes are cut into segments short_div times shorter and
+// taken last: the launch's last warps are short, so it drains quickly.
 void decompose(const dwt2d_plan_s* p, int w_first, int rows, int nl, int rho, int q1,
-               int target_warps, FusedArgs* a, int* grid, int warps_per_block, int segq_fixed = 0) {
+               int target_warps, FusedArgs* a, int* grid, int warps_per_block, int segq_fixed = 0,
+               int resident = 16, int short_div = 0, int seg_f_opt = 0) {
     valid_lanes(nl, rho, q1, &a->lane_lo, &a->lane_hi);
     const int qn = q1 >> (nl - 1);
     const int ppl = qn * (1 << nl);  // input pixels per lane
@@ -239,13 +254,26 @@ void decompose(const dwt2d_plan_s* p, int w_first, int rows, int nl, int rho, in
     if (segq < 1) segq = 1;
     a->segq = segq;
     a->nsegs = (rows + segq - 1) / segq;
+    a->nbig = a->nsegs;
+    a->segq2 = segq;
+    const int res_warps = p->sm_count * resident;
+    if (short_div > 1 && segq_fixed <= 0) {
+        const int sq2 = std::max(std::max(p->min_segq, 1), segq / short_div);
+        const int nshort = std::max(1, res_warps / a->nstrips);  // one wave of short segments
+        const int big = (rows - nshort * sq2) / segq;               // whole long segments above them
+        if (sq2 < segq && big >= 1) {
+            a->nbig = big;
+            a->segq2 = sq2;
+            a->nsegs = big + (rows - big * segq + sq2 - 1) / sq2;
+        }
+    }
     const int items = a->nstrips * a->nsegs;
     *grid = (items + warps_per_block - 1) / warps_per_block;
-    // segments in as many interleaved groups as the launch has waves of
-    // resident warps (16 per SM), so vertically adjacent segments run one
-    // after the other and share their halo rows through L2 (measured 1-2 %)
-    const int resident = p->sm_count * 16;
-    a->seg_f = p->fwd_seg_f > 0 ? p->fwd_seg_f : (items + resident / 2) / resident;
+    // long segments in as many interleaved groups as they fill waves of
+    // resident warps, so vertically adjacent segments run one after the other
+    // and share their halo rows through L2 (measured 1-2 %)
+    const int big_items = a->nstrips * a->nbig;
+    a->seg_f = seg_f_opt > 0 ? seg_f_opt : (big_items + res_warps / 2) / res_warps;
     if (a->seg_f < 1) a->seg_f = 1;
 }
 
@@ -278,7 +306,9 @@ struct GroupLaunch {
 // layout at `ws`; the status word is `err`.
 dwt2d_status build_group(const dwt2d_plan_s* p, bool fwd, int k, const void* src, long long src_pe,
                          void* dst, long long dst_pe, char* ws, int* err, int fwd_target,
-                         int inv_target, GroupLaunch* out, int segq_fixed = 0) {
+                         int inv_target, GroupLaunch* out, int segq_fixed = 0,
+                         bool uniform_segments = false, bool plan_only = false) {
+    const int sch = base_scheme(p->scheme);
     const int elem_kind = elem_kind_of(p->dtype);
     const int rho = p->wavelet == DWT2D_CDF97 ? 2 : 1;
     void* bufs[2] = {ws + p->off_a, ws + p->off_b};
@@ -305,21 +335,46 @@ dwt2d_status build_group(const dwt2d_plan_s* p, bool fwd, int k, const void* src
         a.ll = last ? dst : bufs[gi & 1];
         a.ll_pitch = last ? dst_pe : bpitch[gi & 1];
         a.ll_elems = last ? a.mallat_elems : belems[gi & 1];
-        const int q1 = g.n >= 3 ? 4 : p->fwd_q1;
-        dwt2d_status s = make_map(&out->m[0], in, a.lv[0].h, a.lv[0].w, in_pitch, p->elem, elem_kind,
-                                  64 * q1);
-        if (s != DWT2D_OK) return s;
         const int hN = a.lv[g.n - 1].h;
-        decompose(p, a.lv[0].w, (hN + 1) / 2, g.n, rho, q1, fwd_target, &a, &out->grid, kFwdWarps,
-                  segq_fixed);
-        if (segq_fixed <= 0 && p->fwd_warps_large > fwd_target) {
-            FusedArgs b = a;
-            int grid_b = 0;
-            decompose(p, a.lv[0].w, (hN + 1) / 2, g.n, rho, q1, p->fwd_warps_large, &b, &grid_b,
-                      kFwdWarps);
-            if (b.segq >= p->large_segq) {
-                a = b;
-                out->grid = grid_b;
+        const int rows = (hN + 1) / 2;
+        // quadruple columns per lane: 4 for three fused levels; with
+        // fwd_q1 == 0 (automatic), 4 for a float launch whose rows still give
+        // long segments at the 4-column wave count (measured faster there:
+        // less halo and shuffle work per pixel), else 2
+        int q1 = g.n >= 3 ? 4 : (p->fwd_q1 == 4 ? 4 : 2);
+        FusedArgs big4;
+        int grid4 = 0;
+        bool use4 = false;
+        if (g.n <= 2 && p->fwd_q1 == 0 && segq_fixed <= 0 && elem_kind != 1 && p->fwd_warps_large4 > 0) {
+            big4 = a;
+            decompose(p, a.lv[0].w, rows, g.n, rho, 4, p->fwd_warps_large4, &big4, &grid4, kFwdWarps, 0,
+                      resident_per_sm(true, g.n, 4, sch), uniform_segments ? 0 : p->fwd_short4,
+                      p->fwd_seg_f);
+            use4 = big4.segq >= p->large_segq;
+            if (use4) q1 = 4;
+        }
+        dwt2d_status s = plan_only ? DWT2D_OK
+                                   : make_map(&out->m[0], in, a.lv[0].h, a.lv[0].w, in_pitch, p->elem,
+                                              elem_kind, 64 * q1, fwd_slot_rows(g.n, q1));
+        if (s != DWT2D_OK) return s;
+        if (use4) {
+            a = big4;
+            out->grid = grid4;
+        } else {
+            const int res = resident_per_sm(true, g.n, q1, sch);
+            const int large = q1 == 4 ? p->fwd_warps_large4 : p->fwd_warps_large;
+            const int sd = uniform_segments ? 0 : (q1 == 4 ? p->fwd_short4 : p->fwd_short);
+            decompose(p, a.lv[0].w, rows, g.n, rho, q1, fwd_target, &a, &out->grid, kFwdWarps,
+                      segq_fixed, res, 0, p->fwd_seg_f);
+            if (segq_fixed <= 0 && large > fwd_target) {
+                FusedArgs b = a;
+                int grid_b = 0;
+                decompose(p, a.lv[0].w, rows, g.n, rho, q1, large, &b, &grid_b, kFwdWarps, 0, res, sd,
+                          p->fwd_seg_f);
+                if (b.segq >= p->large_segq) {
+                    a = b;
+                    out->grid = grid_b;
+                }
             }
         }
         out->path = 0;
@@ -352,32 +407,36 @@ dwt2d_status build_group(const dwt2d_plan_s* p, bool fwd, int k, const void* src
         const int q1 = p->inv_q1;
         const int al = 16 / p->elem;  // boxes start at a 16-byte boundary
         const int w1 = 32 * q1 + al, w2 = 16 * q1 + al;
-        dwt2d_status s = make_map(&out->m[0], src, p->H, p->W, src_pe, p->elem, elem_kind, w1, 4);
-        if (s == DWT2D_OK) s = make_map(&out->m[1], src, p->H, p->W, src_pe, p->elem, elem_kind, w2, 2);
+        dwt2d_status s = plan_only ? DWT2D_OK
+                                   : make_map(&out->m[0], src, p->H, p->W, src_pe, p->elem, elem_kind, w1, 4);
+        if (s == DWT2D_OK && !plan_only)
+            s = make_map(&out->m[1], src, p->H, p->W, src_pe, p->elem, elem_kind, w2, 2);
         const int llh = (a.lv[g.n - 1].h + 1) / 2, llw = (a.lv[g.n - 1].w + 1) / 2;
         const bool ll_is_src = k == 0;
-        if (s == DWT2D_OK)
+        if (s == DWT2D_OK && !plan_only)
             s = make_map(&out->m[2], ll_in, ll_is_src ? p->H : llh, ll_is_src ? p->W : llw, ll_pitch,
                          p->elem, elem_kind, g.n == 1 ? w1 : w2, g.n == 1 ? 4 : 2);
         if (s != DWT2D_OK) return s;
+        const int res = resident_per_sm(false, g.n, q1, sch);
+        const int sd = uniform_segments ? 0 : p->inv_short;
+        // the inverse measured fastest with its segments top to bottom
         decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, q1, inv_target, &a, &out->grid,
-                  kInvTmaWarps, segq_fixed);
+                  kInvTmaWarps, segq_fixed, res, 0, p->inv_seg_f);
         if (segq_fixed <= 0 && p->inv_warps_large > inv_target) {
             FusedArgs b = a;
             int grid_b = 0;
             decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, q1, p->inv_warps_large, &b, &grid_b,
-                      kInvTmaWarps);
+                      kInvTmaWarps, 0, res, sd, p->inv_seg_f);
             if (b.segq >= p->large_segq) {
                 a = b;
                 out->grid = grid_b;
             }
         }
-        // the inverse measured fastest with its segments top to bottom
-        if (p->inv_seg_f > 0) a.seg_f = p->inv_seg_f;
         out->path = 1;
         out->q1 = q1;
     } else {
-        decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, 4, inv_target, &a, &out->grid, 4);
+        decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, 4, inv_target, &a, &out->grid, 4, 0,
+                  8, 0, p->inv_seg_f);
         out->path = 2;
         out->q1 = 4;
     }
@@ -607,7 +666,9 @@ static bool options_ok(const dwt2d_plan_options& o) {
            (o.inv_seg_interleave == -1 || in(o.inv_seg_interleave, 1, 1 << 16)) &&
            (o.fwd_cols_per_lane == 0 || o.fwd_cols_per_lane == 2 || o.fwd_cols_per_lane == 4) &&
            (o.inv_cols_per_lane == 0 || o.inv_cols_per_lane == 2 || o.inv_cols_per_lane == 4) &&
-           sw(o.programmatic_launch) && in(o.host_bands, 1, kMaxHostBands) && sw(o.host_pipeline);
+           sw(o.programmatic_launch) && in(o.host_bands, 1, kMaxHostBands) && sw(o.host_pipeline) &&
+           (o.fwd_short_tail == -1 || in(o.fwd_short_tail, 2, 64)) &&
+           (o.inv_short_tail == -1 || in(o.inv_short_tail, 2, 64));
 }
 
 static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width, int32_t levels,
@@ -678,17 +739,25 @@ static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width
     p->min_segq = tuning && tuning->min_segment > 0 ? tuning->min_segment : opt(o.min_segment, 2);
     // measured at 8192^2: the first forward launch is fastest at 48 warps
     // per SM (3 waves of 16) for CDF 9/7 and at 44 for LeGall 5/3 (its
-    // shorter halo), the small later ones at one wave
+    // shorter halo) with 2 columns per lane, at 24 (2 waves of 12) with 4;
+    // the small later ones at one wave
     const int fwl = opt(o.fwd_warps_per_sm_large, wavelet == DWT2D_CDF97 ? 48 : 44);
     p->fwd_warps_large = (tuning && tuning->warps_per_sm > 0) || fwl < 0 ? 0 : sms * fwl;
+    const int fwl4 = opt(o.fwd_warps_per_sm_large, 24);
+    p->fwd_warps_large4 = (tuning && tuning->warps_per_sm > 0) || fwl4 < 0 ? 0 : sms * fwl4;
     p->large_segq = opt(o.large_segment, 16);
     // the finest inverse launch: 64 warps per SM (4 waves of 16)
     const int iwl = opt(o.inv_warps_per_sm_large, 64);
     p->inv_warps_large = (tuning && tuning->warps_per_sm > 0) || iwl < 0 ? 0 : sms * iwl;
-    p->fwd_q1 = o.fwd_cols_per_lane == 4 && !half ? 4 : 2;
+    p->fwd_q1 = o.fwd_cols_per_lane;  // 0: automatic
     p->pdl = opt(o.programmatic_launch, 1) > 0;
     p->fwd_seg_f = o.fwd_seg_interleave;
     p->inv_seg_f = o.inv_seg_interleave < 0 ? 0 : opt(o.inv_seg_interleave, 1);
+    // short last-wave segments: measured 3 % (forward, 3 at 2 columns per
+    // lane, 4 at 4) and 2 % (inverse, 4) faster at 8192^2
+    p->fwd_short = o.fwd_short_tail < 0 ? 0 : opt(o.fwd_short_tail, 3);
+    p->fwd_short4 = o.fwd_short_tail < 0 ? 0 : opt(o.fwd_short_tail, 4);
+    p->inv_short = o.inv_short_tail < 0 ? 0 : opt(o.inv_short_tail, 4);
     p->host_bands = opt(o.host_bands, 8);
     p->host_pipeline = opt(o.host_pipeline, 1) > 0;
     p->inv_q1 = o.inv_cols_per_lane == 4 && !half ? 4 : 2;
@@ -805,7 +874,7 @@ static bool host_resources(dwt2d_plan_s* p) {
 
 // Rows of the first group's input that row segment s reads (its TMA boxes),
 // as the forward kernel computes them: [0, end).
-static int seg_input_end(const dwt2d_plan_s* p, const FusedArgs& a, int nl, int rho, int s) {
+static int seg_input_end(const dwt2d_plan_s* p, const FusedArgs& a, int nl, int q1, int rho, int s) {
     const int neN = (a.lv[nl - 1].h + 1) >> 1;
     const int R0 = s * a.segq, R1 = std::min(R0 + a.segq, neN);
     int f = R0, e = R1 - 1;
@@ -817,9 +886,10 @@ static int seg_input_end(const dwt2d_plan_s* p, const FusedArgs& a, int nl, int 
             e = 2 * e + 1;
         }
     }
-    const int qstart = std::max(f, 0) & ~3, qend = e + 1;
-    const int nslots = (qend - qstart + 3) / 4;
-    return std::min(2 * qstart + kFwdSlotRows * nslots, p->H);
+    const int rows = fwd_slot_rows(nl, q1), sr = rows / 2;  // image / quadruple rows per slot
+    const int qstart = std::max(f, 0) & ~(sr - 1), qend = e + 1;
+    const int nslots = (qend - qstart + sr - 1) / sr;
+    return std::min(2 * qstart + rows * nslots, p->H);
 }
 
 // Host image -> host coefficients with the copies overlapped with the
@@ -868,7 +938,7 @@ static dwt2d_status run_host_fwd_pipelined(dwt2d_plan_s* p, const void* h_src, i
     const int rho = p->wavelet == DWT2D_CDF97 ? 2 : 1;
     GroupLaunch g0;
     dwt2d_status s = build_group(p, true, 0, d_in, dpitch / es, d_out, dpitch / es, wsb, err,
-                                 p->fwd_warps_target, p->inv_warps_target, &g0);
+                                 p->fwd_warps_target, p->inv_warps_target, &g0, 0, true);
     if (s != DWT2D_OK) return s;
     const int nl0 = g0.nl;
     FusedArgs base = g0.a;
@@ -877,12 +947,12 @@ static dwt2d_status run_host_fwd_pipelined(dwt2d_plan_s* p, const void* h_src, i
     for (int c = 0; c < B && next < base.nsegs; ++c) {
         const int avail = std::min((c + 1) * rb, p->H);
         int end = next;
-        while (end < base.nsegs && (c == B - 1 || seg_input_end(p, base, nl0, rho, end) <= avail))
+        while (end < base.nsegs && (c == B - 1 || seg_input_end(p, base, nl0, g0.q1, rho, end) <= avail))
             ++end;
         if (end == next) continue;
         FusedArgs a = base;
         a.seg_lo = next;
-        a.nsegs = end - next;
+        a.nsegs = a.nbig = end - next;
         const int grid = (a.nstrips * a.nsegs + kFwdWarps - 1) / kFwdWarps;
         if (cudaStreamWaitEvent(st, ev_in(c), 0) != cudaSuccess ||
             launch_fwd_fused(elem_kind, sch, nl0, g0.q1, g0.m[0], a, grid, st) != cudaSuccess ||
@@ -1002,7 +1072,7 @@ static dwt2d_status run_host_inv_pipelined(dwt2d_plan_s* p, const void* h_src, i
     }
     GroupLaunch gf;
     dwt2d_status s = build_group(p, false, G - 1, d_in, dpitch / es, d_out, dpitch / es, wsb, err,
-                                 p->fwd_warps_target, p->inv_warps_target, &gf);
+                                 p->fwd_warps_target, p->inv_warps_target, &gf, 0, true);
     if (s != DWT2D_OK) return s;
     if (gf.path != 1) return DWT2D_ERR_INVALID;
     FusedArgs base = gf.a;
@@ -1031,7 +1101,7 @@ static dwt2d_status run_host_inv_pipelined(dwt2d_plan_s* p, const void* h_src, i
         if (end == next) continue;
         FusedArgs a = base;
         a.seg_lo = next;
-        a.nsegs = end - next;
+        a.nsegs = a.nbig = end - next;
         const int grid = (a.nstrips * a.nsegs + kInvTmaWarps - 1) / kInvTmaWarps;
         if (cudaStreamWaitEvent(st, ev_in(c), 0) != cudaSuccess ||
             launch_inv_tma(elem_kind, sch, gf.nl, gf.q1, gf.m[0], gf.m[1], gf.m[2], a, grid, st) !=
@@ -1137,6 +1207,21 @@ dwt2d_status dwt2d_plan_info(dwt2d_plan_t p, int32_t* launches, int32_t* fused, 
     if (n_groups) *n_groups = p->ngroups;
     if (fused)
         for (int g = 0; g < p->ngroups; ++g) fused[g] = p->groups[g].n;
+    return DWT2D_OK;
+}
+
+dwt2d_status dwt2d_plan_launch_info(dwt2d_plan_t p, int32_t inverse, int32_t i, int32_t* fused,
+                                     int32_t* cols_per_lane, int32_t* warps) {
+    if (!p || i < 0 || (inverse != 0 && inverse != 1)) return DWT2D_ERR_INVALID;
+    if (multipass(p->scheme) || (convolution(p->scheme) && !inverse)) return DWT2D_ERR_UNSUPPORTED;
+    if (i >= p->ngroups) return DWT2D_ERR_INVALID;
+    GroupLaunch gl;
+    const dwt2d_status s = build_group(p, !inverse, i, nullptr, 1, nullptr, 1, nullptr, nullptr,
+                                       p->fwd_warps_target, p->inv_warps_target, &gl, 0, false, true);
+    if (s != DWT2D_OK) return s;
+    if (fused) *fused = gl.nl;
+    if (cols_per_lane) *cols_per_lane = gl.q1;
+    if (warps) *warps = gl.a.nstrips * gl.a.nsegs;
     return DWT2D_OK;
 }
 

@@ -248,13 +248,23 @@ __device__ __forceinline__ void copy_arr(T (&d)[Q], const T (&s)[Q]) {
     for (int j = 0; j < Q; ++j) d[j] = s[j];
 }
 
-// Two adjacent columns of a lane as one packed pair, and back.
-template <int Q>
-__device__ __forceinline__ float2 pk(const float (&v)[Q], int j) { return make_float2(v[j], v[j + 1]); }
-template <int Q>
-__device__ __forceinline__ void unpk(float2 p, float (&v)[Q], int j) {
-    v[j] = p.x;
-    v[j + 1] = p.y;
+// Packed (float2) lifting on two columns of a lane at once.  PK selects the
+// pairing: 1 pairs adjacent columns (j, j + 1); 2 pairs columns half a lane
+// apart (j, j + Q/2), so that a pair's right neighbours (j + 1, j + 1 + Q/2)
+// are again a pair for every pair but the last.  pair_head(i) is the first
+// column of pair i (i < Q/2), pk / unpk pack and unpack pair i.
+template <int PK, int Q>
+__device__ __forceinline__ constexpr int pair_head(int i) { return PK == 2 ? i : 2 * i; }
+template <int PK, int Q>
+__device__ __forceinline__ constexpr int pair_step() { return PK == 2 ? Q / 2 : 1; }
+template <int PK, int Q>
+__device__ __forceinline__ float2 pk(const float (&v)[Q], int i) {
+    return make_float2(v[pair_head<PK, Q>(i)], v[pair_head<PK, Q>(i) + pair_step<PK, Q>()]);
+}
+template <int PK, int Q>
+__device__ __forceinline__ void unpk(float2 p, float (&v)[Q], int i) {
+    v[pair_head<PK, Q>(i)] = p.x;
+    v[pair_head<PK, Q>(i) + pair_step<PK, Q>()] = p.y;
 }
 
 // Row segment of the k-th segment slot when segments are taken in F
@@ -274,6 +284,21 @@ __device__ __forceinline__ int seg_order(int k, int nsegs, int f) {
         j = kk % q;
     }
     return j * f + i;
+}
+
+// Rows [r0, r1) of the level a launch's segments are counted in (`rows` in
+// all) for segment slot k (warp id / strips).  The first nbig slots are the
+// segments of segq rows, in interleaved order; later slots are the shorter
+// segments of segq2 rows that follow them, in order, so that the last warps
+// a launch starts are short and the launch drains quickly.
+__device__ __forceinline__ void seg_rows(const FusedArgs& a, int k, int rows, int& r0, int& r1) {
+    if (k < a.nbig) {
+        r0 = (a.seg_lo + seg_order(k, a.nbig, a.seg_f)) * a.segq;
+        r1 = min(r0 + a.segq, rows);
+    } else {
+        r0 = (a.seg_lo + a.nbig) * a.segq + (k - a.nbig) * a.segq2;
+        r1 = min(r0 + a.segq2, rows);
+    }
 }
 
 enum Kind { K_NONE = 0, K_DOWN = 1, K_UP = 2 };
@@ -305,7 +330,7 @@ template <bool EDGE>
 __device__ __forceinline__ bool vact(const LevelCtx& x) { return EDGE ? x.va : true; }
 
 // float, separable (Sec. 2 matrices)
-template <int ID, int SIGN, bool PACK>
+template <int ID, int SIGN, int PK>
 struct OpFTH {
     static constexpr int kind = K_NONE;
     template <bool EDGE, int Q>
@@ -314,13 +339,13 @@ struct OpFTH {
         right_nb<EDGE>(a.c[0], c0r, x.right);
         right_nb<EDGE>(a.c[2], c2r, x.right);
         const float p = hcoef<EDGE>(Coef<ID, SIGN>::v, x);
-        if constexpr (PACK && Q % 2 == 0) {
+        if constexpr (PK != 0 && Q % 2 == 0) {
 #pragma unroll
-            for (int j = 0; j < Q; j += 2) {
-                float2 c1 = pk(a.c[1], j), c3 = pk(a.c[3], j);
-                f_TH(c1, c3, pk(a.c[0], j), pk(c0r, j), pk(a.c[2], j), pk(c2r, j), p);
-                unpk(c1, a.c[1], j);
-                unpk(c3, a.c[3], j);
+            for (int j = 0; j < Q / 2; ++j) {
+                float2 c1 = pk<PK, Q>(a.c[1], j), c3 = pk<PK, Q>(a.c[3], j);
+                f_TH(c1, c3, pk<PK, Q>(a.c[0], j), pk<PK, Q>(c0r, j), pk<PK, Q>(a.c[2], j), pk<PK, Q>(c2r, j), p);
+                unpk<PK, Q>(c1, a.c[1], j);
+                unpk<PK, Q>(c3, a.c[3], j);
             }
         } else {
 #pragma unroll
@@ -328,20 +353,20 @@ struct OpFTH {
         }
     }
 };
-template <int ID, int SIGN, bool PACK>
+template <int ID, int SIGN, int PK>
 struct OpFTV {
     static constexpr int kind = K_DOWN;
     template <bool EDGE, int Q>
     __device__ __forceinline__ static void apply(Quads<float, Q>& a, const float (&n0)[Q],
                                                  const float (&n1)[Q], const LevelCtx& x) {
         const float p = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
-        if constexpr (PACK && Q % 2 == 0) {
+        if constexpr (PK != 0 && Q % 2 == 0) {
 #pragma unroll
-            for (int j = 0; j < Q; j += 2) {
-                float2 c2 = pk(a.c[2], j), c3 = pk(a.c[3], j);
-                f_TV(c2, c3, pk(a.c[0], j), pk(n0, j), pk(a.c[1], j), pk(n1, j), p);
-                unpk(c2, a.c[2], j);
-                unpk(c3, a.c[3], j);
+            for (int j = 0; j < Q / 2; ++j) {
+                float2 c2 = pk<PK, Q>(a.c[2], j), c3 = pk<PK, Q>(a.c[3], j);
+                f_TV(c2, c3, pk<PK, Q>(a.c[0], j), pk<PK, Q>(n0, j), pk<PK, Q>(a.c[1], j), pk<PK, Q>(n1, j), p);
+                unpk<PK, Q>(c2, a.c[2], j);
+                unpk<PK, Q>(c3, a.c[3], j);
             }
         } else {
 #pragma unroll
@@ -349,7 +374,7 @@ struct OpFTV {
         }
     }
 };
-template <int ID, int SIGN, bool PACK>
+template <int ID, int SIGN, int PK>
 struct OpFSH {
     static constexpr int kind = K_NONE;
     template <bool EDGE, int Q>
@@ -362,13 +387,13 @@ struct OpFSH {
         left_nb<EDGE>(a.c[1], c1l, x.left);
         left_nb<EDGE>(a.c[3], c3l, x.left);
         const float u = hcoef<EDGE>(Coef<ID, SIGN>::v, x);
-        if constexpr (PACK && Q % 2 == 0) {
+        if constexpr (PK != 0 && Q % 2 == 0) {
 #pragma unroll
-            for (int j = 0; j < Q; j += 2) {
-                float2 c0 = pk(a.c[0], j), c2 = pk(a.c[2], j);
-                f_SH(c0, c2, pk(a.c[1], j), pk(c1l, j), pk(a.c[3], j), pk(c3l, j), u);
-                unpk(c0, a.c[0], j);
-                unpk(c2, a.c[2], j);
+            for (int j = 0; j < Q / 2; ++j) {
+                float2 c0 = pk<PK, Q>(a.c[0], j), c2 = pk<PK, Q>(a.c[2], j);
+                f_SH(c0, c2, pk<PK, Q>(a.c[1], j), pk<PK, Q>(c1l, j), pk<PK, Q>(a.c[3], j), pk<PK, Q>(c3l, j), u);
+                unpk<PK, Q>(c0, a.c[0], j);
+                unpk<PK, Q>(c2, a.c[2], j);
             }
         } else {
 #pragma unroll
@@ -376,7 +401,7 @@ struct OpFSH {
         }
     }
 };
-template <int ID, int SIGN, bool PACK>
+template <int ID, int SIGN, int PK>
 struct OpFSV {
     static constexpr int kind = K_UP;
     static constexpr bool kHsub = false;
@@ -384,13 +409,13 @@ struct OpFSV {
     __device__ __forceinline__ static void apply(Quads<float, Q>& a, const float (&up2)[Q],
                                                  const float (&up3)[Q], const LevelCtx& x) {
         const float u = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
-        if constexpr (PACK && Q % 2 == 0) {
+        if constexpr (PK != 0 && Q % 2 == 0) {
 #pragma unroll
-            for (int j = 0; j < Q; j += 2) {
-                float2 c0 = pk(a.c[0], j), c1 = pk(a.c[1], j);
-                f_SV(c0, c1, pk(a.c[2], j), pk(up2, j), pk(a.c[3], j), pk(up3, j), u);
-                unpk(c0, a.c[0], j);
-                unpk(c1, a.c[1], j);
+            for (int j = 0; j < Q / 2; ++j) {
+                float2 c0 = pk<PK, Q>(a.c[0], j), c1 = pk<PK, Q>(a.c[1], j);
+                f_SV(c0, c1, pk<PK, Q>(a.c[2], j), pk<PK, Q>(up2, j), pk<PK, Q>(a.c[3], j), pk<PK, Q>(up3, j), u);
+                unpk<PK, Q>(c0, a.c[0], j);
+                unpk<PK, Q>(c1, a.c[1], j);
             }
         } else {
 #pragma unroll
@@ -400,7 +425,7 @@ struct OpFSV {
 };
 
 // float, non-separable (Sec. 3; RED = reduced form)
-template <int ID, int SIGN, bool RED, bool PACK>
+template <int ID, int SIGN, bool RED, int PK>
 struct OpFT {
     static constexpr int kind = K_DOWN;
     template <bool EDGE, int Q>
@@ -411,19 +436,19 @@ struct OpFT {
         right_nb<EDGE>(a.c[2], c2r, x.right);
         right_nb<EDGE>(n0, n0r, x.right);
         const float ph = hcoef<EDGE>(Coef<ID, SIGN>::v, x), pv = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
-        if constexpr (PACK && Q % 2 == 0) {
+        if constexpr (PK != 0 && Q % 2 == 0) {
 #pragma unroll
-            for (int j = 0; j < Q; j += 2) {
-                float2 c1 = pk(a.c[1], j), c2 = pk(a.c[2], j), c3 = pk(a.c[3], j);
+            for (int j = 0; j < Q / 2; ++j) {
+                float2 c1 = pk<PK, Q>(a.c[1], j), c2 = pk<PK, Q>(a.c[2], j), c3 = pk<PK, Q>(a.c[3], j);
                 if (RED)
-                    f_T_red(c1, c2, c3, pk(a.c[0], j), pk(c0r, j), pk(c2r, j), pk(n0, j), pk(n1, j),
-                            pk(n0r, j), ph, pv);
+                    f_T_red(c1, c2, c3, pk<PK, Q>(a.c[0], j), pk<PK, Q>(c0r, j), pk<PK, Q>(c2r, j), pk<PK, Q>(n0, j), pk<PK, Q>(n1, j),
+                            pk<PK, Q>(n0r, j), ph, pv);
                 else
-                    f_T_plain(c1, c2, c3, pk(a.c[0], j), pk(c0r, j), pk(c2r, j), pk(n0, j), pk(n1, j),
-                              pk(n0r, j), ph, pv);
-                unpk(c1, a.c[1], j);
-                unpk(c2, a.c[2], j);
-                unpk(c3, a.c[3], j);
+                    f_T_plain(c1, c2, c3, pk<PK, Q>(a.c[0], j), pk<PK, Q>(c0r, j), pk<PK, Q>(c2r, j), pk<PK, Q>(n0, j), pk<PK, Q>(n1, j),
+                              pk<PK, Q>(n0r, j), ph, pv);
+                unpk<PK, Q>(c1, a.c[1], j);
+                unpk<PK, Q>(c2, a.c[2], j);
+                unpk<PK, Q>(c3, a.c[3], j);
             }
         } else {
 #pragma unroll
@@ -438,7 +463,7 @@ struct OpFT {
         }
     }
 };
-template <int ID, int SIGN, bool RED, bool PACK>
+template <int ID, int SIGN, bool RED, int PK>
 struct OpFS {
     static constexpr int kind = K_UP;
     static constexpr bool kHsub = true;
@@ -450,19 +475,19 @@ struct OpFS {
         left_nb<EDGE>(a.c[3], c3l, x.left);
         left_nb<EDGE>(up3, u3l, x.left);
         const float uh = hcoef<EDGE>(Coef<ID, SIGN>::v, x), uv = vcoef<EDGE>(Coef<ID, SIGN>::v, x);
-        if constexpr (PACK && Q % 2 == 0) {
+        if constexpr (PK != 0 && Q % 2 == 0) {
 #pragma unroll
-            for (int j = 0; j < Q; j += 2) {
-                float2 c0 = pk(a.c[0], j), c1 = pk(a.c[1], j), c2 = pk(a.c[2], j);
+            for (int j = 0; j < Q / 2; ++j) {
+                float2 c0 = pk<PK, Q>(a.c[0], j), c1 = pk<PK, Q>(a.c[1], j), c2 = pk<PK, Q>(a.c[2], j);
                 if (RED)
-                    f_S_red(c0, c1, c2, pk(a.c[3], j), pk(c1l, j), pk(c3l, j), pk(up2, j), pk(up3, j),
-                            pk(u3l, j), uh, uv);
+                    f_S_red(c0, c1, c2, pk<PK, Q>(a.c[3], j), pk<PK, Q>(c1l, j), pk<PK, Q>(c3l, j), pk<PK, Q>(up2, j), pk<PK, Q>(up3, j),
+                            pk<PK, Q>(u3l, j), uh, uv);
                 else
-                    f_S_plain(c0, c1, c2, pk(a.c[3], j), pk(c1l, j), pk(c3l, j), pk(up2, j),
-                              pk(up3, j), pk(u3l, j), uh, uv);
-                unpk(c0, a.c[0], j);
-                unpk(c1, a.c[1], j);
-                unpk(c2, a.c[2], j);
+                    f_S_plain(c0, c1, c2, pk<PK, Q>(a.c[3], j), pk<PK, Q>(c1l, j), pk<PK, Q>(c3l, j), pk<PK, Q>(up2, j),
+                              pk<PK, Q>(up3, j), pk<PK, Q>(u3l, j), uh, uv);
+                unpk<PK, Q>(c0, a.c[0], j);
+                unpk<PK, Q>(c1, a.c[1], j);
+                unpk<PK, Q>(c2, a.c[2], j);
             }
         } else {
 #pragma unroll
@@ -720,41 +745,49 @@ template <class T, int Q, int SCH, bool FWD>
 struct Pipe;
 
 // CDF 9/7 forward: pairs (alpha, beta), (gamma, delta).  The forward runs the
-// scalar form of the float steps, the inverse the packed (float2) form: each
-// measured faster for its kernel (the forward kernel's register budget of 128
-// leaves no room for the register pairs).
+// scalar form of the float steps at 2 columns per lane (its register budget of
+// 128 leaves no room for the register pairs) and the packed form at 4
+// (kFwdPack4: 1 adjacent, 2 strided pairs); the inverse runs the packed form
+// on adjacent pairs.  Each was measured faster for its kernel.
+#ifndef DWT_FWD_PACK4
+#define DWT_FWD_PACK4 2
+#endif
+constexpr int kFwdPack4 = DWT_FWD_PACK4;
+template <int Q>
+constexpr int fwd_pk() { return Q >= 4 ? kFwdPack4 : 0; }
 template <int Q>
 struct Pipe<float, Q, SCH_SEP, true> {
-    using type = Chain<float, Q, OpFTH<0, 1, false>, OpFTV<0, 1, false>, OpFSH<1, 1, false>,
-                       OpFSV<1, 1, false>, OpFTH<2, 1, false>, OpFTV<2, 1, false>,
-                       OpFSH<3, 1, false>, OpFSV<3, 1, false>>;
+    static constexpr int P = fwd_pk<Q>();
+    using type = Chain<float, Q, OpFTH<0, 1, P>, OpFTV<0, 1, P>, OpFSH<1, 1, P>, OpFSV<1, 1, P>,
+                       OpFTH<2, 1, P>, OpFTV<2, 1, P>, OpFSH<3, 1, P>, OpFSV<3, 1, P>>;
 };
 template <int Q>
 struct Pipe<float, Q, SCH_NONSEP, true> {
-    using type = Chain<float, Q, OpFT<0, 1, false, false>, OpFS<1, 1, false, false>,
-                       OpFT<2, 1, false, false>, OpFS<3, 1, false, false>>;
+    static constexpr int P = fwd_pk<Q>();
+    using type = Chain<float, Q, OpFT<0, 1, false, P>, OpFS<1, 1, false, P>, OpFT<2, 1, false, P>,
+                       OpFS<3, 1, false, P>>;
 };
 template <int Q>
 struct Pipe<float, Q, SCH_RED, true> {
-    using type = Chain<float, Q, OpFT<0, 1, true, false>, OpFS<1, 1, true, false>,
-                       OpFT<2, 1, true, false>, OpFS<3, 1, true, false>>;
+    static constexpr int P = fwd_pk<Q>();
+    using type = Chain<float, Q, OpFT<0, 1, true, P>, OpFS<1, 1, true, P>, OpFT<2, 1, true, P>,
+                       OpFS<3, 1, true, P>>;
 };
 // CDF 9/7 inverse: undo every step in reverse order.
 template <int Q>
 struct Pipe<float, Q, SCH_SEP, false> {
-    using type = Chain<float, Q, OpFSV<3, -1, true>, OpFSH<3, -1, true>, OpFTV<2, -1, true>,
-                       OpFTH<2, -1, true>, OpFSV<1, -1, true>, OpFSH<1, -1, true>,
-                       OpFTV<0, -1, true>, OpFTH<0, -1, true>>;
+    using type = Chain<float, Q, OpFSV<3, -1, 1>, OpFSH<3, -1, 1>, OpFTV<2, -1, 1>, OpFTH<2, -1, 1>,
+                       OpFSV<1, -1, 1>, OpFSH<1, -1, 1>, OpFTV<0, -1, 1>, OpFTH<0, -1, 1>>;
 };
 template <int Q>
 struct Pipe<float, Q, SCH_NONSEP, false> {
-    using type = Chain<float, Q, OpFS<3, -1, false, true>, OpFT<2, -1, false, true>,
-                       OpFS<1, -1, false, true>, OpFT<0, -1, false, true>>;
+    using type = Chain<float, Q, OpFS<3, -1, false, 1>, OpFT<2, -1, false, 1>,
+                       OpFS<1, -1, false, 1>, OpFT<0, -1, false, 1>>;
 };
 template <int Q>
 struct Pipe<float, Q, SCH_RED, false> {
-    using type = Chain<float, Q, OpFS<3, -1, true, true>, OpFT<2, -1, true, true>,
-                       OpFS<1, -1, true, true>, OpFT<0, -1, true, true>>;
+    using type = Chain<float, Q, OpFS<3, -1, true, 1>, OpFT<2, -1, true, 1>,
+                       OpFS<1, -1, true, 1>, OpFT<0, -1, true, 1>>;
 };
 // LeGall 5/3 (reversible): the reduced scheme keeps the floors on whole 1-D
 // sums and is therefore the same integer dataflow as the non-separable one.
@@ -783,9 +816,12 @@ struct Pipe<int, Q, SCH_RED, false> {
     using type = Chain<int, Q, OpIS<false>, OpIT<false>>;
 };
 
-// CDF 9/7 scale of LL, HL, LH, HH when both axes are active: 1/K^2, 1, 1, K^2.
-constexpr float kScaleLL = 1.0f / (kK * kK);
-constexpr float kScaleHH = kK * kK;
+// CDF 9/7 scale of LL, HL, LH, HH when both axes are active: 1/K^2, 1, 1, K^2,
+// rounded once from double, exactly as the host rounds the per-level scales
+// the border code uses (so both code paths give the same bits).
+constexpr double kKd = 1.230174104914001;
+constexpr float kScaleLL = (float)(1.0 / (kKd * kKd));
+constexpr float kScaleHH = (float)(kKd * kKd);
 
 // One level of the transform for one warp: the chain plus the 9/7 scaling.
 template <class T, int Q, int SCH, bool FWD>

@@ -33,6 +33,17 @@ __device__ __forceinline__ void store_cols(S* p, const T (&v)[Q], int avail, boo
     }
 }
 
+// Border-free store of a lane's Q values at p: every column lies inside its
+// band and p is vector aligned; ok = the lane stores and the row belongs to
+// the work item (one predicate, no branches per column).
+template <class S, class T, int Q>
+__device__ __forceinline__ void st_fast(S* p, const T (&v)[Q], bool ok) {
+    S w[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) w[j] = Storage<S>::st(v[j]);
+    if (ok && store_ok(p, Q * (int)sizeof(S))) st_vec<S, Q>(p, w);
+}
+
 // Per-level store state of one lane.
 struct StoreGeo {
     int ne_r, no_r, ne_c, no_c;
@@ -109,6 +120,12 @@ __device__ __forceinline__ void pair_rows(const T (&e)[Q], const T (&o)[Q], Quad
     }
 }
 
+// Quadruple rows per slot (one TMA box of 2 SR image rows): 4, or 2 with 4
+// columns per lane and at most 2 fused levels (the same 8 quadruples per
+// lane per lifting step, and a box of the same bytes).
+template <int NL, int Q1>
+__host__ __device__ constexpr int fwd_slot_quads() { return (Q1 >= 4 && NL <= 2) ? 2 : 4; }
+
 // All state of one warp's work item: the level engines, per-level geometry and
 // the pending even LL rows, plus the static per-slot schedule.  Q1 quadruple
 // columns per lane at level 1 (2 Q1 pixels), Q1/2 at level 2, Q1/4 at level 3.
@@ -119,6 +136,8 @@ struct FwdWarp {
     static constexpr int Q2 = Q1 / 2 > 0 ? Q1 / 2 : 1;
     static constexpr int Q3 = Q1 / 4 > 0 ? Q1 / 4 : 1;
     static constexpr int BW = 64 * Q1;  // box width in pixels
+    static constexpr int SR = fwd_slot_quads<NL, Q1>();  // quadruple rows per slot
+    static_assert(NL <= 2 || SR == 4, "three fused levels need slots of 4 quadruple rows");
     Engine<T, Q1, SCH, true> e1;
     Engine<T, Q2, SCH, true> e2;
     Engine<T, Q3, SCH, true> e3;
@@ -131,15 +150,16 @@ struct FwdWarp {
     bool lane_ok, vec_ll;
     int lane;
 
-    // One slot: level-1 input quadruple rows q0 .. q0+3 (q0 a multiple of 4) in
-    // shared memory (8 image rows of BW pixels), pushed as one block.  With
-    // q0 % 4 == 0 the rows every level emits, and how LL rows pair into the
-    // next level's quadruple rows, are fixed by the pipeline lag alone.
+    // One slot: level-1 input quadruple rows q0 .. q0+SR-1 (q0 a multiple of
+    // SR) in shared memory (2 SR image rows of BW pixels), pushed as one
+    // block.  With q0 % SR == 0 the rows every level emits, and how LL rows
+    // pair into the next level's quadruple rows, are fixed by the pipeline lag
+    // alone.
     template <bool EDGE>
     __device__ __forceinline__ void slot(const S* sm, int q0) {
-        Block<T, Q1, 4> b1;
+        Block<T, Q1, SR> b1;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < SR; ++k) {
             Quads<T, Q1>& row = b1.r[k];
             S ev[2 * Q1], od[2 * Q1];
             ld_vec<S, 2 * Q1>(ev, sm + (2 * k) * BW + 2 * Q1 * lane);
@@ -152,16 +172,35 @@ struct FwdWarp {
                 row.c[3][j] = Storage<S>::ld(od[2 * j + 1]);
             }
         }
-        e1.template push<EDGE, 4>(b1, q0, x1);
+        e1.template push<EDGE, SR>(b1, q0, x1);
         const int r1 = q0 - LAG;  // first emitted level-1 row
-        {
+        if constexpr (!EDGE) {
+            // border-free slot: band addresses advanced by the pitch, one
+            // predicate per row
+            S* hl = mallat + (long long)r1 * mpitch + (s1.g0 + s1.ne_c);
+            S* lh = hl + ((long long)s1.ne_r * mpitch - s1.ne_c);
+            S* lrow = ll + (long long)r1 * llpitch + s1.g0;
+#pragma unroll
+            for (int k = 0; k < SR; ++k) {
+                const bool ok = lane_ok && r1 + k >= s1.r_lo && r1 + k < s1.r_hi;
+                st_fast<S, T, Q1>(hl, b1.r[k].c[1], ok);
+                st_fast<S, T, Q1>(lh, b1.r[k].c[2], ok);
+                st_fast<S, T, Q1>(lh + s1.ne_c, b1.r[k].c[3], ok);
+                hl += mpitch;
+                lh += mpitch;
+                if constexpr (NL == 1) {
+                    st_fast<S, T, Q1>(lrow, b1.r[k].c[0], ok);
+                    lrow += llpitch;
+                }
+            }
+        } else {
             // one row address per slot, advanced by the pitch (bands of row r
             // at base, base + ne_c, base + ne_r pitch (+ ne_c))
             S* base = mallat + (long long)r1 * mpitch + s1.g0;
             const long long dlh = (long long)s1.ne_r * mpitch;
             S* lrow = ll + (long long)r1 * llpitch + s1.g0;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < SR; ++k) {
                 store_details_at<S, T, Q1>(b1.r[k], r1 + k, s1, base, dlh, lane_ok);
                 base += mpitch;
                 if constexpr (NL == 1) {
@@ -171,25 +210,44 @@ struct FwdWarp {
             }
         }
         if constexpr (NL >= 2) {
-            // level-2 input rows q0/2 - 1 and q0/2 = LL rows q0 - 2 .. q0 + 1
-            Block<T, Q2, 2> b2;
-            if constexpr (LAG == 2) {  // emitted rows q0-2 .. q0+1
-                pair_rows<T, Q1>(b1.r[0].c[0], b1.r[1].c[0], b2.r[0]);
-                pair_rows<T, Q1>(b1.r[2].c[0], b1.r[3].c[0], b2.r[1]);
-            } else {  // emitted rows q0-1 .. q0+2; row q0-2 was kept from the last slot
+            // level-2 input rows q0/2 - 1 .. q0/2 + R2 - 2 = LL rows q0 - 2 .. q0 + SR - 3
+            constexpr int R2 = SR / 2;
+            Block<T, Q2, R2> b2;
+            if constexpr (LAG == 2) {  // emitted rows q0-2 .. q0+SR-3
+#pragma unroll
+                for (int j = 0; j < R2; ++j) pair_rows<T, Q1>(b1.r[2 * j].c[0], b1.r[2 * j + 1].c[0], b2.r[j]);
+            } else {  // emitted rows q0-1 .. q0+SR-2; row q0-2 was kept from the last slot
                 pair_rows<T, Q1>(pend1, b1.r[0].c[0], b2.r[0]);
-                pair_rows<T, Q1>(b1.r[1].c[0], b1.r[2].c[0], b2.r[1]);
-                copy_arr(pend1, b1.r[3].c[0]);
+#pragma unroll
+                for (int j = 1; j < R2; ++j) pair_rows<T, Q1>(b1.r[2 * j - 1].c[0], b1.r[2 * j].c[0], b2.r[j]);
+                copy_arr(pend1, b1.r[SR - 1].c[0]);
             }
             const int in2 = q0 / 2 - 1;
-            e2.template push<EDGE, 2>(b2, in2, x2);
+            e2.template push<EDGE, R2>(b2, in2, x2);
             const int r2 = in2 - LAG;
-            {
+            if constexpr (!EDGE) {
+                S* hl = mallat + (long long)r2 * mpitch + (s2.g0 + s2.ne_c);
+                S* lh = hl + ((long long)s2.ne_r * mpitch - s2.ne_c);
+                S* lrow = ll + (long long)r2 * llpitch + s2.g0;
+#pragma unroll
+                for (int k = 0; k < R2; ++k) {
+                    const bool ok = lane_ok && r2 + k >= s2.r_lo && r2 + k < s2.r_hi;
+                    st_fast<S, T, Q2>(hl, b2.r[k].c[1], ok);
+                    st_fast<S, T, Q2>(lh, b2.r[k].c[2], ok);
+                    st_fast<S, T, Q2>(lh + s2.ne_c, b2.r[k].c[3], ok);
+                    hl += mpitch;
+                    lh += mpitch;
+                    if constexpr (NL == 2) {
+                        st_fast<S, T, Q2>(lrow, b2.r[k].c[0], ok);
+                        lrow += llpitch;
+                    }
+                }
+            } else {
                 S* base = mallat + (long long)r2 * mpitch + s2.g0;
                 const long long dlh = (long long)s2.ne_r * mpitch;
                 S* lrow = ll + (long long)r2 * llpitch + s2.g0;
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
+                for (int k = 0; k < R2; ++k) {
                     store_details_at<S, T, Q2>(b2.r[k], r2 + k, s2, base, dlh, lane_ok);
                     base += mpitch;
                     if constexpr (NL == 2) {
@@ -218,11 +276,11 @@ struct FwdWarp {
     }
 };
 
-// Rows of level l pushed in the slot of level-1 rows [q0, q0 + 4) lie in
+// Rows of level l pushed in the slot of level-1 rows [q0, q0 + sr) lie in
 // [lo, hi]; the interior code is valid if every stage row touched is at least
 // one row away from the top and stays clear of the last odd row.
-__device__ __forceinline__ bool rows_interior(int q0, int nl, int lag, const int* no_r) {
-    int lo = q0, hi = q0 + 3;
+__device__ __forceinline__ bool rows_interior(int q0, int sr, int nl, int lag, const int* no_r) {
+    int lo = q0, hi = q0 + sr - 1;
     for (int l = 0; l < nl; ++l) {
         if (lo - lag - 1 < 0 || hi + 1 >= no_r[l]) return false;
         lo = floordiv2(lo - lag) - 1;
@@ -231,10 +289,13 @@ __device__ __forceinline__ bool rows_interior(int q0, int nl, int lag, const int
     return true;
 }
 
-template <int Q1>
 // CTAs per SM the register budget is sized for: 16 warps (128 registers) with
-// 2 quadruple columns per lane, 8 warps with 4.
-__host__ __device__ constexpr int fwd_min_blocks() { return (Q1 <= 2 ? 16 : 8) / kFwdWarps; }
+// 2 quadruple columns per lane; with 4, 12 warps (168 registers) for slots of
+// 2 quadruple rows, 8 for three fused levels.
+template <int NL, int Q1>
+__host__ __device__ constexpr int fwd_min_blocks() {
+    return (Q1 <= 2 ? 16 : (fwd_slot_quads<NL, Q1>() == 2 ? 12 : 8)) / kFwdWarps;
+}
 
 // One warp's work item `wid` of a launch described by `a` (input through the
 // tensor map at `mapp`).
@@ -245,25 +306,26 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArg
     using T = typename FW::T;
     constexpr int RHO = FW::LAG;
     constexpr int BW = FW::BW;
+    constexpr int SR = FW::SR;
+    constexpr int SLOT_ROWS = 2 * SR;  // image rows per TMA box
     static_assert(Engine<T, Q1, SCH, true>::LAG == RHO && Engine<T, 1, SCH, true>::LAG == RHO, "lag");
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
 
-    constexpr int kSlotElems = kFwdSlotRows * BW;
+    constexpr int kSlotElems = SLOT_ROWS * BW;
     S* ring = reinterpret_cast<S*>(smem_raw) + (size_t)warp * kFwdSlots * kSlotElems;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kFwdWarps * kFwdSlots *
                                                               kSlotElems * sizeof(S)) +
                      warp * kFwdSlots;
 
     const int strip = wid % a.nstrips;
-    const int seg = a.seg_lo + seg_order(wid / a.nstrips, a.nsegs, a.seg_f);
     const int xb = strip * a.valid_px - a.xoff;
 
     // rows of the last fused level this item produces, and the input rows it needs
     const int neN = (a.lv[NL - 1].h + 1) >> 1;
-    const int R0 = seg * a.segq;
-    const int R1 = min(R0 + a.segq, neN);
+    int R0, R1;
+    seg_rows(a, wid / a.nstrips, neN, R0, R1);
     int f = R0, e = R1 - 1;
 #pragma unroll
     for (int l = NL; l >= 1; --l) {
@@ -274,9 +336,9 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArg
             e = 2 * e + 1;
         }
     }
-    const int qstart = max(f, 0) & ~3;  // slots hold 4 quadruple rows, aligned
+    const int qstart = max(f, 0) & ~(SR - 1);  // slots hold SR quadruple rows, aligned
     const int qend = e + 1;
-    const int nslots = (qend - qstart + 3) / 4;
+    const int nslots = (qend - qstart + SR - 1) / SR;
 
     FW W;
     W.lane = lane;
@@ -310,6 +372,10 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArg
         no_r[2] = a.lv[2].h >> 1;
         hfast = hfast && (xb >> 3) >= 2 && (xb >> 3) + 32 * FW::Q3 + 2 <= (a.lv[2].w >> 1);
     }
+    // the border-free code stores whole vectors only
+    hfast = hfast && W.s1.vec_hl && W.s1.vec_lh && W.vec_ll;
+    if constexpr (NL >= 2) hfast = hfast && W.s2.vec_hl && W.s2.vec_lh;
+    if constexpr (NL >= 3) hfast = hfast && W.s3.vec_hl && W.s3.vec_lh;
     W.e1.init();
     if constexpr (NL >= 2) W.e2.init();
     if constexpr (NL >= 3) W.e3.init();
@@ -326,7 +392,7 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArg
         fence_mbar_init();
         for (int s = 0; s < kFwdSlots && s < nslots; ++s) {
             mbar_arrive_expect_tx(bar_s + 8 * s, kSlotBytes);
-            tma_load_2d(ring_s + s * kSlotBytes, mapp, xb, y0 + s * kFwdSlotRows, bar_s + 8 * s);
+            tma_load_2d(ring_s + s * kSlotBytes, mapp, xb, y0 + s * SLOT_ROWS, bar_s + 8 * s);
         }
     }
     __syncwarp();
@@ -340,8 +406,8 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArg
             failed = true;
             break;
         }
-        const int q0 = qstart + 4 * s;
-        if (hfast && rows_interior(q0, NL, RHO, no_r))
+        const int q0 = qstart + SR * s;
+        if (hfast && rows_interior(q0, SR, NL, RHO, no_r))
             W.template slot<false>(ring + b * kSlotElems, q0);
         else
             W.template slot<true>(ring + b * kSlotElems, q0);
@@ -349,7 +415,7 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArg
         if (lane == 0 && s + kFwdSlots < nslots) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar_s + 8 * b, kSlotBytes);
-            tma_load_2d(ring_s + b * kSlotBytes, mapp, xb, y0 + (s + kFwdSlots) * kFwdSlotRows,
+            tma_load_2d(ring_s + b * kSlotBytes, mapp, xb, y0 + (s + kFwdSlots) * SLOT_ROWS,
                         bar_s + 8 * b);
         }
     }
@@ -362,7 +428,7 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArg
 }
 
 template <class S, int SCH, int NL, int Q1>
-__global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<Q1>())
+__global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<NL, Q1>())
     fwd_fused_kernel(const __grid_constant__ CUtensorMap map, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     grid_dependency_sync();
@@ -395,8 +461,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12 / kFwdWarps)
     fwd_body<S, SCH, NL, Q1>(&e.m[0], a, wid, smem_raw);
 }
 
-size_t fwd_smem_bytes(int elem_bytes, int q1) {
-    return (size_t)kFwdWarps * kFwdSlots * kFwdSlotRows * (64 * q1) * elem_bytes +
+int fwd_slot_rows(int nl, int q1) { return 2 * ((q1 >= 4 && nl <= 2) ? 2 : 4); }
+
+size_t fwd_smem_bytes(int elem_bytes, int nl, int q1) {
+    return (size_t)kFwdWarps * kFwdSlots * fwd_slot_rows(nl, q1) * (64 * q1) * elem_bytes +
            (size_t)kFwdWarps * kFwdSlots * 8;
 }
 
@@ -404,7 +472,7 @@ template <class S, int SCH, int NL, int Q1>
 static cudaError_t launch_one(const CUtensorMap& map, const FusedArgs& a, int grid,
                               cudaStream_t st) {
     auto k = fwd_fused_kernel<S, SCH, NL, Q1>;
-    const size_t smem = fwd_smem_bytes(sizeof(S), Q1);
+    const size_t smem = fwd_smem_bytes(sizeof(S), NL, Q1);
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     return launch_kernel(k, grid, kFwdWarps * 32, smem, st, a.pdl != 0, map, a);
@@ -414,7 +482,7 @@ template <class S, int SCH, int NL>
 static cudaError_t launch_batched_one(const BatchEntry* table, int n, int grid, cudaStream_t st,
                                       bool pdl) {
     auto k = fwd_batched_kernel<S, SCH, NL, 2>;
-    const size_t smem = fwd_smem_bytes(sizeof(S), 2);
+    const size_t smem = fwd_smem_bytes(sizeof(S), NL, 2);
     if (grid == 0)
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch_kernel(k, grid, kFwdWarps * 32, smem, st, pdl, table, n);
@@ -475,18 +543,24 @@ static cudaError_t launch_sch(int sch, int nl, int q1, const CUtensorMap& map, c
     return cudaErrorInvalidValue;
 }
 
-// 16-bit storage: 1 or 2 fused levels, 2 columns per lane
+// 16-bit storage: 1 or 2 fused levels, 2 or 4 columns per lane
+template <class S, int SCH>
+static cudaError_t launch_nl16(int nl, int q1, const CUtensorMap& map, const FusedArgs& a, int grid,
+                               cudaStream_t st) {
+    if (nl == 1) return q1 == 4 ? launch_one<S, SCH, 1, 4>(map, a, grid, st)
+                                : launch_one<S, SCH, 1, 2>(map, a, grid, st);
+    if (nl == 2) return q1 == 4 ? launch_one<S, SCH, 2, 4>(map, a, grid, st)
+                                : launch_one<S, SCH, 2, 2>(map, a, grid, st);
+    return cudaErrorInvalidValue;
+}
+
 template <class S>
-static cudaError_t launch_sch16(int sch, int nl, const CUtensorMap& map, const FusedArgs& a,
+static cudaError_t launch_sch16(int sch, int nl, int q1, const CUtensorMap& map, const FusedArgs& a,
                                 int grid, cudaStream_t st) {
-    if (nl < 1 || nl > 2) return cudaErrorInvalidValue;
     switch (sch) {
-        case SCH_SEP: return nl == 1 ? launch_one<S, SCH_SEP, 1, 2>(map, a, grid, st)
-                                     : launch_one<S, SCH_SEP, 2, 2>(map, a, grid, st);
-        case SCH_NONSEP: return nl == 1 ? launch_one<S, SCH_NONSEP, 1, 2>(map, a, grid, st)
-                                        : launch_one<S, SCH_NONSEP, 2, 2>(map, a, grid, st);
-        case SCH_RED: return nl == 1 ? launch_one<S, SCH_RED, 1, 2>(map, a, grid, st)
-                                     : launch_one<S, SCH_RED, 2, 2>(map, a, grid, st);
+        case SCH_SEP: return launch_nl16<S, SCH_SEP>(nl, q1, map, a, grid, st);
+        case SCH_NONSEP: return launch_nl16<S, SCH_NONSEP>(nl, q1, map, a, grid, st);
+        case SCH_RED: return launch_nl16<S, SCH_RED>(nl, q1, map, a, grid, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -496,9 +570,9 @@ cudaError_t launch_fwd_fused(int elem, int scheme, int nl, int q1, const CUtenso
     switch (elem) {
         case 0: return launch_sch<float>(scheme, nl, q1, map, a, grid, st);
         case 1: return launch_sch<int>(scheme, nl, q1, map, a, grid, st);
-        // 16-bit storage: up to 2 fused levels with 2 columns per lane
-        case 2: return launch_sch16<__half>(scheme, nl, map, a, grid, st);
-        case 3: return launch_sch16<__nv_bfloat16>(scheme, nl, map, a, grid, st);
+        // 16-bit storage: up to 2 fused levels
+        case 2: return launch_sch16<__half>(scheme, nl, q1, map, a, grid, st);
+        case 3: return launch_sch16<__nv_bfloat16>(scheme, nl, q1, map, a, grid, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -35,6 +35,10 @@ struct FusedArgs {
     int nstrips, nsegs, segq;        // warp work items = nstrips * nsegs
     int seg_f;                       // segment order interleave (<= 1: top to bottom)
     int seg_lo;                      // first row segment of this launch (launches over a subset)
+    // segments [0, nbig) have segq rows (taken in seg_f interleaved groups);
+    // segments [nbig, nsegs) are shorter, segq2 rows each, below them, taken
+    // last and top to bottom (nbig == nsegs: every segment has segq rows)
+    int nbig, segq2;
     long long mallat_elems, ll_elems, out_elems;  // buffer extents (elements) for checked builds
     int valid_px, xoff;              // strip width in input pixels and left halo offset
     int lane_lo, lane_hi;            // lanes that store
@@ -75,9 +79,12 @@ struct BatchEntry {
 // scheduler refill an SM warp by warp (measured 1-4 % faster than 4)
 constexpr int kFwdWarps = 1;
 constexpr int kFwdSlots = 3;        // TMA ring depth per warp
-constexpr int kFwdSlotRows = 8;     // image rows per TMA box (4 quadruple rows)
+constexpr int kFwdSlotRows = 8;     // image rows per TMA box (4 quadruple rows) with 2 columns per lane
 
-size_t fwd_smem_bytes(int elem_bytes, int q1);
+// Image rows per TMA box of the forward kernel: 8, or 4 with 4 quadruple
+// columns per lane and at most 2 fused levels.
+int fwd_slot_rows(int nl, int q1);
+size_t fwd_smem_bytes(int elem_bytes, int nl, int q1);
 
 // Batched forward / inverse: entries of one element type, scheme and fusion
 // depth (1 or 2), 2 quadruple columns per lane; `grid` CTAs of kFwdWarps

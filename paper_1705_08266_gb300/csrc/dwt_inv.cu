@@ -173,7 +173,6 @@ __global__ void __launch_bounds__(128) inv_fused_kernel(const FusedArgs a) {
     const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (wid >= a.nstrips * a.nsegs) return;
     const int strip = wid % a.nstrips;
-    const int seg = wid / a.nstrips;
 
     InvWarp<T, SCH, NL> W;
     W.lane = lane;
@@ -188,8 +187,7 @@ __global__ void __launch_bounds__(128) inv_fused_kernel(const FusedArgs a) {
     W.vec_out = (a.out_pitch % 4) == 0;
     set_store_windows(a.out, a.out_elems * (long long)sizeof(T), nullptr, 0, a.err);
     const int ne1 = (a.lv[0].h + 1) >> 1;
-    W.A0 = seg * a.segq;
-    W.A1 = min(W.A0 + a.segq, ne1);
+    seg_rows(a, wid / a.nstrips, ne1, W.A0, W.A1);
 
 #pragma unroll
     for (int l = 0; l < NL; ++l) {

@@ -176,7 +176,6 @@ __device__ __forceinline__ void inv_body(const CUtensorMap* m1p, const CUtensorM
                      warp * kInvSlots;
 
     const int strip = wid % a.nstrips;
-    const int seg = a.seg_lo + seg_order(wid / a.nstrips, a.nsegs, a.seg_f);
     W w;
     w.lane = lane;
     w.xb = strip * a.valid_px - a.xoff;
@@ -190,8 +189,7 @@ __device__ __forceinline__ void inv_body(const CUtensorMap* m1p, const CUtensorM
     set_store_windows(a.out, a.out_elems * (long long)sizeof(S), nullptr, 0, a.err);
     w.vec_row = w.vec_out && w.x0l >= 0 && w.x0l + 2 * Q1 <= a.lv[0].w;
     const int ne1 = (a.lv[0].h + 1) >> 1;
-    w.A0 = seg * a.segq;
-    w.A1 = min(w.A0 + a.segq, ne1);
+    seg_rows(a, wid / a.nstrips, ne1, w.A0, w.A1);
 
     int no_r[2] = {a.lv[0].h >> 1, NL >= 2 ? (a.lv[1].h >> 1) : 0};
     const int g1w = w.xb >> 1;

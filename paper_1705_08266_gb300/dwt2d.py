@@ -60,7 +60,7 @@ class PlanOptions(ctypes.Structure):
         "fuse_first", "fuse_max", "fwd_warps_per_sm", "inv_warps_per_sm", "fwd_warps_per_sm_large",
         "inv_warps_per_sm_large", "large_segment", "min_segment", "fwd_seg_interleave",
         "inv_seg_interleave", "fwd_cols_per_lane", "inv_cols_per_lane", "programmatic_launch",
-        "host_bands", "host_pipeline")]
+        "host_bands", "host_pipeline", "fwd_short_tail", "inv_short_tail")]
 
 
 def plan_options(**kw) -> PlanOptions:
@@ -101,6 +101,9 @@ def lib() -> ctypes.CDLL:
     L.dwt2d_workspace_init.argtypes = [vp, vp]
     L.dwt2d_workspace_status.argtypes = [vp, vp]
     L.dwt2d_plan_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.dwt2d_plan_launch_info.argtypes = [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                         ctypes.POINTER(i32)]
+    L.dwt2d_plan_launch_info.restype = ctypes.c_int
     L.dwt2d_plan_set_launch_events.argtypes = [vp, ctypes.POINTER(vp), i32]
     L.dwt2d_plan_set_launch_events.restype = ctypes.c_int
     L.dwt2d_plan_destroy.argtypes = [vp]
@@ -196,6 +199,17 @@ class Plan:
         fused = (ctypes.c_int32 * 16)()
         _check(lib().dwt2d_plan_info(self._h, ctypes.byref(n), fused, ctypes.byref(ng)), "plan_info")
         return n.value, [fused[i] for i in range(ng.value)]
+
+    def launch_info(self, inverse: bool = False):
+        """[(levels fused, columns per lane, warps)] of each launch of a call, in launch order."""
+        out = []
+        n = self.info()[0]
+        for i in range(n):
+            f, q, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+            _check(lib().dwt2d_plan_launch_info(self._h, int(inverse), i, ctypes.byref(f), ctypes.byref(q),
+                                                ctypes.byref(w)), "plan_launch_info")
+            out.append((f.value, q.value, w.value))
+        return out
 
     def set_launch_events(self, events):
         """Record events[2i] / events[2i+1] (torch.cuda.Event) around launch i of later calls."""

@@ -183,3 +183,22 @@ def test_plan_options_change_the_launch_decomposition_only(L):
         assert L.dwt2d_plan_info(p, ctypes.byref(n), fused, ctypes.byref(ng)) == 0
         assert [fused[i] for i in range(ng.value)] == groups
         L.dwt2d_plan_destroy(p)
+
+
+def test_plan_launch_info_reports_the_chosen_shapes(L):
+    """The forward's first launch of a large float image runs 4 quadruple
+    columns per lane, the small later ones 2; LeGall 5/3 keeps 2; forcing the
+    columns is honoured; the multipass schemes have no streaming launches."""
+    p = D.Plan(8192, 8192, 5, "cdf97", "nonsep_reduced")
+    shapes = p.launch_info()
+    assert [f for f, _q, _w in shapes] == [2, 2, 1]
+    assert shapes[0][1] == 4 and shapes[1][1] == 2 and shapes[2][1] == 2
+    assert all(w > 0 for _f, _q, w in shapes)
+    assert [f for f, _q, _w in p.launch_info(inverse=True)] == [1, 2, 2]
+    assert D.Plan(8192, 8192, 5, "legall53", "nonsep").launch_info()[0][1] == 2
+    assert D.Plan(8192, 8192, 5, "cdf97", "nonsep_reduced",
+                  options={"fwd_cols_per_lane": 2}).launch_info()[0][1] == 2
+    assert D.Plan(512, 512, 2, "cdf97", "nonsep_reduced",
+                  options={"fwd_cols_per_lane": 4}).launch_info()[0][1] == 4
+    with pytest.raises(D.DwtError):
+        D.Plan(512, 512, 2, "cdf97", "nonsep_multipass").launch_info()

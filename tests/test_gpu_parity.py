@@ -257,3 +257,51 @@ def test_host_pipelined_band_counts(bands, h, w, levels, wavelet, dtype):
     torch.cuda.synchronize()
     assert torch.equal(back, ref_back.cpu())
     assert plan.status(ws) == 0
+
+
+LAUNCH_OPTIONS = [
+    {"fwd_cols_per_lane": 4},
+    {"fwd_cols_per_lane": 4, "fwd_short_tail": 4, "fwd_warps_per_sm_large": 24},
+    {"fwd_short_tail": 3, "inv_short_tail": 4},
+    {"fwd_cols_per_lane": 4, "fwd_short_tail": 2, "min_segment": 1, "fwd_warps_per_sm": 4000,
+     "inv_short_tail": 2, "inv_warps_per_sm": 4000},
+    {"fwd_cols_per_lane": 4, "fuse_first": 1, "fwd_seg_interleave": 1, "inv_seg_interleave": -1},
+]
+
+
+@pytest.mark.parametrize("opts", LAUNCH_OPTIONS, ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()))
+@pytest.mark.parametrize("wavelet,dtype", [("cdf97", torch.float32), ("legall53", torch.int32),
+                                           ("cdf97", torch.float16)])
+def test_launch_options_give_the_same_bits(opts, wavelet, dtype):
+    """Launch options change how the rows are cut into launches, warps and
+    segments (columns per lane, short last-wave segments, interleave, fusion),
+    not the arithmetic: every setting gives the default plan's bits, forward
+    and inverse, and the default plan matches the oracle.  (With 16-bit
+    storage the LL between launches is rounded to 16 bits, so a different
+    fusion depth is checked against the tolerance instead.)"""
+    regroups = "fuse_first" in opts or "fuse_max" in opts
+    for (h, w), levels in [((1030, 2050), 5), ((2048, 1536), 3), ((777, 3001), 2), ((301, 497), 4),
+                           ((4099, 520), 6)]:
+        x = make_input(wavelet, h, w, seed=h * 5 + w)
+        scale = 1.0
+        if dtype == torch.float16:
+            scale = float(np.max(np.abs(x)))
+            x = x / scale
+        xt = torch.from_numpy(x).to(dtype)
+        res = []
+        for o in ({}, opts):
+            plan = D.Plan(h, w, levels, wavelet, "nonsep_reduced", dtype, options=o or None)
+            ws = plan.workspace()
+            c = plan.forward(_dev16(xt), workspace=ws, scale=scale)
+            y = plan.inverse(c, workspace=ws, scale=scale)
+            torch.cuda.synchronize()
+            assert plan.status(ws) == 0
+            res.append((c.cpu(), y.cpu()))
+        if dtype == torch.float16 and regroups:
+            d = (res[0][0].float() - res[1][0].float()).abs().max().item()
+            assert d <= 2e-3, (opts, h, w, levels, d)
+            continue
+        assert torch.equal(res[0][0], res[1][0]), (opts, h, w, levels, "forward")
+        assert torch.equal(res[0][1], res[1][1]), (opts, h, w, levels, "inverse")
+        if dtype != torch.float16:
+            assert_forward_matches(res[0][0].numpy(), x, levels, wavelet, f"{h}x{w} L{levels}")
