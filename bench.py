@@ -417,6 +417,8 @@ def main():
         out["precision_16384x16384_l6"] = precision_variants(D, synth, dev, stream)
         out["batch_256_mixed"] = batch_variants(D, synth, dev, stream)
         out["serving_poisson"] = serving_variant(D, synth, dev)
+        # the same recipe at ten times the arrival rate: batches fill up
+        out["serving_poisson_10x"] = serving_variant(D, synth, dev, seconds=3.0, rate=20000.0)
 
     if args.no_e2e:
         if rank == 0:
@@ -647,6 +649,27 @@ def batch_variants(D, synth, dev, stream):
             ms = time_calls(g.replay, iters, stream)
         res[name] = {"ms": round(ms, 4), "gpx_s": round(px / ms / 1e6, 1)}
         del g
+    # the persistent form: one launch per direction and storage type over a
+    # queue of every level group's work items
+    pb = D.Batch(jobs, tuning={"persistent": 1})
+    pws = pb.workspace(dev)
+    pb.upload(pws, stream=stream)
+    fn = lambda: pb.launch(pws, stream=stream)  # noqa: E731
+    for _ in range(warm):
+        fn()
+    ms = time_calls(fn, iters, stream)
+    res["batch_persistent_eager"] = {"ms": round(ms, 4), "gpx_s": round(px / ms / 1e6, 1),
+                                     "launches": pb.info()[0]}
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        fn()
+    with torch.cuda.stream(stream):
+        for _ in range(warm):
+            g.replay()
+        ms = time_calls(g.replay, iters, stream)
+    res["batch_persistent_graph"] = {"ms": round(ms, 4), "gpx_s": round(px / ms / 1e6, 1)}
+    assert pb.status(pws, stream=stream) == 0
+    del g
     with tempfile.TemporaryDirectory() as tmp:
         best = autotune.tune(jobs, cache_path=os.path.join(tmp, "tune.json"), stream=stream)
     tb = D.Batch(jobs, tuning=best)
@@ -721,16 +744,20 @@ def serving_variant(D, synth, dev, seconds: float = 10.0, rate: float = 2000.0):
     gc.enable()
     st = srv.stats()
     srv.close()
-    return {"workload": "Poisson 2000/s for 10 s; s log-uniform [64, 8192], aspect U[1,4], short side "
-                        ">= 16; 70% fwd / 30% inv; levels U{1..6}; 50% CDF 9/7 f16 / 50% LeGall 5/3 "
-                        "i32; 40 GB budget; seed 2026; device-resident inputs",
+    return {"workload": f"Poisson {rate:.0f}/s for {seconds:g} s; s log-uniform [64, 8192], aspect U[1,4], "
+                        "short side >= 16; 70% fwd / 30% inv; levels U{1..6}; 50% CDF 9/7 f16 / 50% "
+                        "LeGall 5/3 i32; 40 GB budget; seed 2026; device-resident inputs; "
+                        f"{len(srv.ex.streams)} streams",
             "requests": n, "pixels": px, "completed": st["completed"], "rejected": st["rejected"],
             "failed": st["failed"], "wall_s": round(wall, 3),
             "p50_ms": round(st["p50_s"] * 1e3, 3) if st["p50_s"] is not None else None,
             "p99_ms": round(st["p99_s"] * 1e3, 3) if st["p99_s"] is not None else None,
             "max_ms": round(st["max_s"] * 1e3, 3) if st["max_s"] is not None else None,
             "requests_per_s": round(st["completed"] / wall, 1), "gpx_s": round(px / wall / 1e9, 3),
-            "batches": st["batches"], "peak_reserved_gb": round(st["peak_bytes"] / 1e9, 3)}
+            "batches": st["batches"],
+            "requests_per_batch": round(st["requests_per_batch"], 2) if st["requests_per_batch"] else None,
+            "max_requests_per_batch": st["max_batch_seen"],
+            "peak_reserved_gb": round(st["peak_bytes"] / 1e9, 3)}
 
 
 if __name__ == "__main__":

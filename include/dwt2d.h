@@ -348,6 +348,11 @@ typedef struct {
 typedef struct {
     int32_t fuse_first, fuse_max, warps_per_sm, min_segment;
     int32_t programmatic_launch;
+    int32_t persistent;  /* 1: one persistent launch per direction and storage type over a
+                            queue of every level group's work items (warps take items from a
+                            counter; an item waits, bounded, until the level group it reads
+                            is done); otherwise one launch per level group, direction,
+                            storage type and fusion depth */
 } dwt2d_tuning;
 
 /*
@@ -360,9 +365,10 @@ typedef struct {
  * dwt2d_batch_upload -- write the descriptor tables into d_workspace
  *   (asynchronous on stream; not capturable: call it before any capture).
  *   Zeroes the status word.
- * dwt2d_batch_launch -- launch every kernel of the batch on stream; kernel
- *   launches only, so it can be captured in a CUDA graph and replayed.  The
- *   workspace must have been uploaded for this batch.
+ * dwt2d_batch_launch -- launch every kernel of the batch on stream (in the
+ *   persistent form, after one memset of the queue counters); nothing else,
+ *   so it can be captured in a CUDA graph and replayed.  The workspace must
+ *   have been uploaded for this batch.
  * dwt2d_batch_info -- kernel launches per dwt2d_batch_launch and warps in all.
  */
 dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* items, int32_t n,

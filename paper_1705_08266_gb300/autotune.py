@@ -1,9 +1,12 @@
 """Autotuner for batched transforms (dwt2d_batch_*).
 
-A batch's launch shape has four knobs (dwt2d_tuning): levels fused in an
-image's first launch, levels fused per later launch, warps targeted per SM
-(how finely the rows of one launch are cut into warp segments, i.e. how many
-waves), and the smallest segment.  The best setting depends on the mix of
+A batch's launch shape has five knobs (dwt2d_tuning): levels fused in an
+image's first launch, levels fused per later launch (with the wavelet, this
+sets the halo each strip and segment recomputes), warps targeted per SM (how
+finely the rows are cut into warp segments, i.e. how many waves or queue
+items), the smallest segment, and the launch form (one launch per level group
+and kind, or one persistent launch per direction and storage type over a
+queue of work items).  The best setting depends on the mix of
 image sizes and level counts, so the tuner times a small set of candidates on
 the batch itself (CUDA events, on the caller's buffers: the outputs are
 overwritten) and keeps the fastest.  Results are cached in a JSON file keyed
@@ -18,11 +21,14 @@ import json
 import os
 from typing import Callable, Iterable, Optional
 
-KNOBS = ("fuse_first", "fuse_max", "warps_per_sm", "min_segment")
+KNOBS = ("fuse_first", "fuse_max", "warps_per_sm", "min_segment", "persistent")
 
 CANDIDATES = [
-    {"fuse_first": ff, "fuse_max": 2, "warps_per_sm": w, "min_segment": m}
+    {"fuse_first": ff, "fuse_max": 2, "warps_per_sm": w, "min_segment": m, "persistent": 0}
     for ff in (2, 1) for w in (12, 24, 32, 48) for m in (2, 8)
+] + [
+    {"fuse_first": 2, "fuse_max": 2, "warps_per_sm": w, "min_segment": m, "persistent": 1}
+    for w in (24, 48, 96) for m in (2, 8)
 ]
 
 

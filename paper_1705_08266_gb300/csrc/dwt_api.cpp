@@ -84,6 +84,21 @@ struct dwt2d_batch_s {
     std::vector<dwt::BatchEntry> table;      // host copy, filled at upload
     size_t table_off, ws_bytes;
     long long warps;
+    // queue mode: one persistent launch per (direction, storage type) over a
+    // queue of every level group's work items; qtable holds the entries queue
+    // by queue (table index order within a queue), counters the queue heads
+    // and one done counter per (image, level group)
+    bool queue;
+    struct Queue {
+        int fwd, elem_kind;
+        int first, count;  // entries [first, first + count) of qtable
+        long long items;
+    };
+    std::vector<Queue> queues;
+    std::vector<int> qorder;                 // qtable entry -> table entry
+    std::vector<dwt::BatchEntry> qtable;
+    size_t qtable_off, counters_off, counters_bytes;
+    int max_groups, sms;
     ~dwt2d_batch_s() {
         for (auto* p : plans) free(p);
     }
@@ -1259,6 +1274,7 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
     if (!b) return DWT2D_ERR_NOMEM;
     b->scheme = scheme;
     b->pdl = tun.programmatic_launch > 0;  // default off: measured neutral to 1 % slower for batches
+    b->queue = tun.persistent > 0;
     b->items.assign(items, items + n);
     size_t off = kHeader;
     b->table_off = off;
@@ -1351,6 +1367,26 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
         }
     }
     off += (b->refs.size() * sizeof(BatchEntry) + 255) / 256 * 256;
+    b->max_groups = max_groups;
+    b->sms = sms;
+    // queues: the launches of one (direction, storage type), in launch order
+    // (level group by level group)
+    for (int fwd = 1; fwd >= 0; --fwd) {
+        for (int ek = 0; ek < 4; ++ek) {
+            dwt2d_batch_s::Queue q = {fwd, ek, (int)b->qorder.size(), 0, 0};
+            for (const auto& L : b->launches) {
+                if (L.fwd != fwd || L.elem_kind != ek) continue;
+                for (int j = L.first; j < L.first + L.count; ++j) b->qorder.push_back(j);
+            }
+            q.count = (int)b->qorder.size() - q.first;
+            if (q.count > 0) b->queues.push_back(q);
+        }
+    }
+    b->qtable_off = off;
+    off += (b->qorder.size() * sizeof(BatchEntry) + 255) / 256 * 256;
+    b->counters_off = off;
+    b->counters_bytes = (size_t)(8 + n * std::max(max_groups, 1)) * sizeof(int);
+    off += (b->counters_bytes + 255) / 256 * 256;
     for (int i = 0; i < n; ++i) {
         b->region.push_back(off);
         off += (b->plans[i]->ws_bytes + 255) / 256 * 256;
@@ -1396,6 +1432,43 @@ dwt2d_status dwt2d_batch_upload(dwt2d_batch_t b, void* d_ws, void* stream) {
         cudaMemcpyAsync(wsb + b->table_off, b->table.data(), b->table.size() * sizeof(BatchEntry),
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
         return DWT2D_ERR_CUDA;
+    // queue mode: the same entries queue by queue, numbered within their
+    // queue, with their done counters and the group each depends on
+    b->qtable.clear();
+    std::vector<long long> items_of((size_t)b->items.size() * std::max(b->max_groups, 1), 0);
+    for (size_t j = 0; j < b->table.size(); ++j) {
+        const int i = b->refs[j].first, k = b->refs[j].second;
+        items_of[(size_t)i * b->max_groups + k] =
+            (long long)b->table[j].args.nstrips * b->table[j].args.nsegs;
+    }
+    for (auto& q : b->queues) {
+        long long first = 0;
+        for (int t = q.first; t < q.first + q.count; ++t) {
+            const int j = b->qorder[t];
+            const int i = b->refs[j].first, k = b->refs[j].second;
+            BatchEntry e = b->table[j];
+            e.first_warp = (int)first;
+            e.self = i * b->max_groups + k;
+            e.dep = k > 0 ? i * b->max_groups + (k - 1) : -1;
+            e.dep_items = k > 0 ? (int)items_of[(size_t)i * b->max_groups + (k - 1)] : 0;
+            for (const auto& L : b->launches)
+                if (j >= L.first && j < L.first + L.count) e.nl = L.nl;
+            first += (long long)e.args.nstrips * e.args.nsegs;
+            b->qtable.push_back(e);
+        }
+        q.items = first;
+        if (first > (1LL << 30)) return DWT2D_ERR_INVALID;
+        const int sch = base_scheme(b->scheme);
+        const cudaError_t e = q.fwd ? launch_fwd_queue(q.elem_kind, sch, nullptr, 0, 0, nullptr, nullptr,
+                                                       nullptr, 0, st)
+                                    : launch_inv_queue(q.elem_kind, sch, nullptr, 0, 0, nullptr, nullptr,
+                                                       nullptr, 0, st);
+        if (e != cudaSuccess) return DWT2D_ERR_CUDA;
+    }
+    if (!b->qtable.empty() &&
+        cudaMemcpyAsync(wsb + b->qtable_off, b->qtable.data(), b->qtable.size() * sizeof(BatchEntry),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return DWT2D_ERR_CUDA;
     if (cudaMemsetAsync(d_ws, 0, sizeof(int), st) != cudaSuccess) return DWT2D_ERR_CUDA;
     return DWT2D_OK;
 }
@@ -1408,6 +1481,27 @@ dwt2d_status dwt2d_batch_launch(dwt2d_batch_t b, void* d_ws, void* stream) {
     const BatchEntry* table =
         reinterpret_cast<const BatchEntry*>(reinterpret_cast<char*>(d_ws) + b->table_off);
     const int sch = base_scheme(b->scheme);
+    if (b->queue) {
+        char* wsb = reinterpret_cast<char*>(d_ws);
+        int* err = reinterpret_cast<int*>(wsb);
+        int* heads = reinterpret_cast<int*>(wsb + b->counters_off);
+        int* done = heads + 8;
+        // counters start at zero on every launch (a memset node in a captured graph)
+        if (cudaMemsetAsync(heads, 0, b->counters_bytes, st) != cudaSuccess) return DWT2D_ERR_CUDA;
+        const BatchEntry* qt = reinterpret_cast<const BatchEntry*>(wsb + b->qtable_off);
+        const long long resident = (long long)b->sms * 12;  // the queue kernels' register budget
+        for (size_t qi = 0; qi < b->queues.size(); ++qi) {
+            const auto& q = b->queues[qi];
+            const int grid = (int)std::min<long long>(q.items, resident);
+            const cudaError_t e =
+                q.fwd ? launch_fwd_queue(q.elem_kind, sch, qt + q.first, q.count, (int)q.items,
+                                         heads + qi, done, err, grid, st)
+                      : launch_inv_queue(q.elem_kind, sch, qt + q.first, q.count, (int)q.items,
+                                         heads + qi, done, err, grid, st);
+            if (e != cudaSuccess) return DWT2D_ERR_CUDA;
+        }
+        return DWT2D_OK;
+    }
     for (const auto& L : b->launches) {
         const cudaError_t e =
             L.fwd ? launch_fwd_batched(L.elem_kind, sch, L.nl, table + L.first, L.count, L.grid, st, b->pdl)
@@ -1419,7 +1513,7 @@ dwt2d_status dwt2d_batch_launch(dwt2d_batch_t b, void* d_ws, void* stream) {
 
 dwt2d_status dwt2d_batch_info(dwt2d_batch_t b, int32_t* launches, int64_t* warps) {
     if (!b) return DWT2D_ERR_INVALID;
-    if (launches) *launches = (int32_t)b->launches.size();
+    if (launches) *launches = (int32_t)(b->queue ? b->queues.size() : b->launches.size());
     if (warps) *warps = b->warps;
     return DWT2D_OK;
 }

@@ -299,8 +299,9 @@ __host__ __device__ constexpr int fwd_min_blocks() {
 
 // One warp's work item `wid` of a launch described by `a` (input through the
 // tensor map at `mapp`).
+// Returns false if a bounded wait gave up (the status word is set).
 template <class S, int SCH, int NL, int Q1>
-__device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArgs& a, int wid,
+__device__ __forceinline__ bool fwd_body(const CUtensorMap* mapp, const FusedArgs& a, int wid,
                                          unsigned char* smem_raw) {
     using FW = FwdWarp<S, SCH, NL, Q1>;
     using T = typename FW::T;
@@ -424,7 +425,13 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* mapp, const FusedArg
         // drain the copies still in flight before the warp leaves
         for (int t = s; t < nslots && t < s + kFwdSlots; ++t)
             mbar_wait_bounded(bar_s + 8 * (t % kFwdSlots), (t / kFwdSlots) & 1, kWaitBudget);
+        return false;
     }
+    // every copy has landed: the barriers may be initialised again
+    if (lane == 0)
+        for (int b = 0; b < kFwdSlots; ++b) mbar_inval(bar_s + 8 * b);
+    __syncwarp();
+    return true;
 }
 
 template <class S, int SCH, int NL, int Q1>
@@ -462,6 +469,91 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12 / kFwdWarps)
 }
 
 int fwd_slot_rows(int nl, int q1) { return 2 * ((q1 >= 4 && nl <= 2) ? 2 : 4); }
+
+// Binary search: the last entry with first_warp <= g.
+__device__ __forceinline__ int find_entry(const BatchEntry* __restrict__ table, int n, int g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (table[mid].first_warp <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Persistent form: every warp takes work items from the queue until it is
+// empty.  Items are ordered by level group, so every item an item depends on
+// was taken earlier by a running warp: the bounded wait always ends unless a
+// warp failed, and then the status word already says so.
+template <class S, int SCH>
+__global__ void __launch_bounds__(kFwdWarps * 32, 12 / kFwdWarps)
+    fwd_queue_kernel(const BatchEntry* __restrict__ table, int n, int total, int* head, int* done,
+                     int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    grid_dependency_sync();
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(head, 1);
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= total) break;
+        const BatchEntry& e = table[find_entry(table, n, g)];
+        const FusedArgs a = e.args;
+        const int wid = g - e.first_warp;
+        bool ok = true;
+        if (e.dep >= 0) {
+            if (lane == 0) {
+                ok = wait_counter_bounded(done + e.dep, e.dep_items, kWaitBudget);
+                if (ok) fence_proxy_async_global();
+                else atomicExch(err, -6);
+            }
+            ok = __shfl_sync(kFull, ok ? 1 : 0, 0) != 0;
+        }
+        if (ok) {
+            fence_tensormap_acquire(&e.m[0]);
+            ok = e.nl == 2 ? fwd_body<S, SCH, 2, 2>(&e.m[0], a, wid, smem_raw)
+                           : fwd_body<S, SCH, 1, 2>(&e.m[0], a, wid, smem_raw);
+        }
+        __syncwarp();
+        if (!ok) break;  // copies may still be in flight: stop using the ring
+        if (lane == 0) {
+            __threadfence();  // this item's stores before its count
+            atomicAdd(done + e.self, 1);
+        }
+    }
+}
+
+template <class S, int SCH>
+static cudaError_t launch_queue_one(const BatchEntry* table, int n, int total, int* head, int* done,
+                                    int* err, int grid, cudaStream_t st) {
+    auto k = fwd_queue_kernel<S, SCH>;
+    const size_t smem = fwd_smem_bytes(sizeof(S), 2, 2);
+    if (grid == 0)
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch_kernel(k, grid, kFwdWarps * 32, smem, st, false, table, n, total, head, done, err);
+}
+
+template <class S>
+static cudaError_t launch_queue_s(int sch, const BatchEntry* table, int n, int total, int* head,
+                                  int* done, int* err, int grid, cudaStream_t st) {
+    switch (sch) {
+        case SCH_SEP: return launch_queue_one<S, SCH_SEP>(table, n, total, head, done, err, grid, st);
+        case SCH_NONSEP: return launch_queue_one<S, SCH_NONSEP>(table, n, total, head, done, err, grid, st);
+        case SCH_RED: return launch_queue_one<S, SCH_RED>(table, n, total, head, done, err, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fwd_queue(int elem, int scheme, const BatchEntry* table, int n, int total, int* head,
+                             int* done, int* err, int grid, cudaStream_t st) {
+    switch (elem) {
+        case 0: return launch_queue_s<float>(scheme, table, n, total, head, done, err, grid, st);
+        case 1: return launch_queue_s<int>(scheme, table, n, total, head, done, err, grid, st);
+        case 2: return launch_queue_s<__half>(scheme, table, n, total, head, done, err, grid, st);
+        case 3: return launch_queue_s<__nv_bfloat16>(scheme, table, n, total, head, done, err, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
 
 size_t fwd_smem_bytes(int elem_bytes, int nl, int q1) {
     return (size_t)kFwdWarps * kFwdSlots * fwd_slot_rows(nl, q1) * (64 * q1) * elem_bytes +

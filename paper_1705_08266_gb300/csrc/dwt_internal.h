@@ -71,8 +71,21 @@ struct PassArgs {
 struct BatchEntry {
     CUtensorMap m[3];
     FusedArgs args;
-    int first_warp;  // first global warp of this entry in the launch
+    int first_warp;  // first global warp of this entry in the launch (queue mode: in its queue)
+    // queue mode: the entry's fusion depth, its done counter (image, level
+    // group) and the counter of the group it consumes (-1: none) with the
+    // number of work items that group has
+    int nl, self, dep, dep_items;
 };
+
+// Persistent batched kernels (queue mode): `grid` one-warp CTAs take the
+// `total` work items of a queue (entries of one direction and storage type,
+// every level group, ordered by group) through the counter `head`; an item of
+// a later group first waits (bounded) until done[dep] reaches dep_items.
+cudaError_t launch_fwd_queue(int elem, int scheme, const BatchEntry* table, int n, int total,
+                             int* head, int* done, int* err, int grid, cudaStream_t st);
+cudaError_t launch_inv_queue(int elem, int scheme, const BatchEntry* table, int n, int total,
+                             int* head, int* done, int* err, int grid, cudaStream_t st);
 
 // Kernel-geometry constants of the streaming forward kernel.
 // warps per CTA: each warp is independent, so one-warp CTAs let the CTA

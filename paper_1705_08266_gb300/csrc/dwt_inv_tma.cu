@@ -156,8 +156,9 @@ __device__ __forceinline__ bool inv_rows_interior(int q0, int nl, int lag, const
     return true;
 }
 
+// Returns false if a bounded wait gave up (the status word is set).
 template <class S, int SCH, int NL, int Q1>
-__device__ __forceinline__ void inv_body(const CUtensorMap* m1p, const CUtensorMap* m2p,
+__device__ __forceinline__ bool inv_body(const CUtensorMap* m1p, const CUtensorMap* m2p,
                                          const CUtensorMap* mlp, const FusedArgs& a, int wid,
                                          unsigned char* smem_raw) {
     using W = InvWarpT<S, SCH, NL, Q1>;
@@ -286,7 +287,13 @@ __device__ __forceinline__ void inv_body(const CUtensorMap* m1p, const CUtensorM
         if (lane == 0) atomicExch(a.err, -6);
         for (int t = s; t < nslots && t < s + kInvSlots; ++t)
             mbar_wait_bounded(bar_s + 8 * (t % kInvSlots), (t / kInvSlots) & 1, kWaitBudget);
+        return false;
     }
+    // every copy has landed: the barriers may be initialised again
+    if (lane == 0)
+        for (int b = 0; b < kInvSlots; ++b) mbar_inval(bar_s + 8 * b);
+    __syncwarp();
+    return true;
 }
 
 // 16 warps per SM (128 registers) with 2 quadruple columns per lane, 8 with 4;
@@ -325,6 +332,88 @@ __global__ void __launch_bounds__(kInvWarps * 32, (Q1 <= 2 ? 12 : 8) / kInvWarps
     fence_tensormap_acquire(&e.m[1]);
     fence_tensormap_acquire(&e.m[2]);
     inv_body<S, SCH, NL, Q1>(&e.m[0], &e.m[1], &e.m[2], a, wid, smem_raw);
+}
+
+// Persistent form over a queue of work items (see fwd_queue_kernel).
+template <class S, int SCH>
+__global__ void __launch_bounds__(kInvWarps * 32, 12 / kInvWarps)
+    inv_queue_kernel(const BatchEntry* __restrict__ table, int n, int total, int* head, int* done,
+                     int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    grid_dependency_sync();
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(head, 1);
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= total) break;
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (table[mid].first_warp <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchEntry& e = table[lo];
+        const FusedArgs a = e.args;
+        const int wid = g - e.first_warp;
+        bool ok = true;
+        if (e.dep >= 0) {
+            if (lane == 0) {
+                ok = wait_counter_bounded(done + e.dep, e.dep_items, kWaitBudget);
+                if (ok) fence_proxy_async_global();
+                else atomicExch(err, -6);
+            }
+            ok = __shfl_sync(kFull, ok ? 1 : 0, 0) != 0;
+        }
+        if (ok) {
+            fence_tensormap_acquire(&e.m[0]);
+            fence_tensormap_acquire(&e.m[1]);
+            fence_tensormap_acquire(&e.m[2]);
+            ok = e.nl == 2 ? inv_body<S, SCH, 2, 2>(&e.m[0], &e.m[1], &e.m[2], a, wid, smem_raw)
+                           : inv_body<S, SCH, 1, 2>(&e.m[0], &e.m[1], &e.m[2], a, wid, smem_raw);
+        }
+        __syncwarp();
+        if (!ok) break;  // copies may still be in flight: stop using the ring
+        if (lane == 0) {
+            __threadfence();  // this item's stores before its count
+            atomicAdd(done + e.self, 1);
+        }
+    }
+}
+
+template <class S, int SCH>
+static cudaError_t inv_queue_one(const BatchEntry* table, int n, int total, int* head, int* done,
+                                 int* err, int grid, cudaStream_t st) {
+    auto k = inv_queue_kernel<S, SCH>;
+    // the larger ring of the two fusion depths
+    const size_t smem = inv_tma_smem_bytes(sizeof(S), 2, 2) > inv_tma_smem_bytes(sizeof(S), 1, 2)
+                            ? inv_tma_smem_bytes(sizeof(S), 2, 2)
+                            : inv_tma_smem_bytes(sizeof(S), 1, 2);
+    if (grid == 0)
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch_kernel(k, grid, kInvWarps * 32, smem, st, false, table, n, total, head, done, err);
+}
+
+template <class S>
+static cudaError_t inv_queue_s(int sch, const BatchEntry* table, int n, int total, int* head, int* done,
+                               int* err, int grid, cudaStream_t st) {
+    switch (sch) {
+        case SCH_SEP: return inv_queue_one<S, SCH_SEP>(table, n, total, head, done, err, grid, st);
+        case SCH_NONSEP: return inv_queue_one<S, SCH_NONSEP>(table, n, total, head, done, err, grid, st);
+        case SCH_RED: return inv_queue_one<S, SCH_RED>(table, n, total, head, done, err, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_inv_queue(int elem, int scheme, const BatchEntry* table, int n, int total, int* head,
+                             int* done, int* err, int grid, cudaStream_t st) {
+    switch (elem) {
+        case 0: return inv_queue_s<float>(scheme, table, n, total, head, done, err, grid, st);
+        case 1: return inv_queue_s<int>(scheme, table, n, total, head, done, err, grid, st);
+        case 2: return inv_queue_s<__half>(scheme, table, n, total, head, done, err, grid, st);
+        case 3: return inv_queue_s<__nv_bfloat16>(scheme, table, n, total, head, done, err, grid, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 size_t inv_tma_smem_bytes(int elem_bytes, int nl, int q1) {

@@ -14,6 +14,32 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
+// Invalidate a barrier whose phases have all completed, before it is
+// initialised again for another work item.
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Data another thread wrote with ordinary stores and published through an
+// acquired flag: order that acquire before this thread's later TMA reads of
+// global memory.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Wait until *flag >= target (acquire, GPU scope); give up after `budget`
+// clock cycles.  Spins with a short sleep between reads.
+__device__ __forceinline__ bool wait_counter_bounded(const int* flag, int target, long long budget) {
+    const long long t0 = clock64();
+    for (;;) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v >= target) return true;
+        if (clock64() - t0 > budget) return false;
+        __nanosleep(256);
+    }
+}
+
 // Make initialised barriers visible to the async (TMA) proxy.
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

@@ -51,7 +51,7 @@ class Tuning(ctypes.Structure):
     """dwt2d_tuning (0 = library default)."""
     _fields_ = [("fuse_first", ctypes.c_int32), ("fuse_max", ctypes.c_int32),
                 ("warps_per_sm", ctypes.c_int32), ("min_segment", ctypes.c_int32),
-                ("programmatic_launch", ctypes.c_int32)]
+                ("programmatic_launch", ctypes.c_int32), ("persistent", ctypes.c_int32)]
 
 
 class PlanOptions(ctypes.Structure):
@@ -304,7 +304,7 @@ class Batch:
         if tuning is not None:
             tun = ctypes.byref(Tuning(*[int(tuning.get(k, 0)) for k in
                                         ("fuse_first", "fuse_max", "warps_per_sm", "min_segment",
-                                         "programmatic_launch")]))
+                                         "programmatic_launch", "persistent")]))
         self._h = ctypes.c_void_p()
         ws = ctypes.c_size_t()
         _check(L.dwt2d_batch_create(ctypes.byref(self._h), arr, len(self.jobs), SCHEMES[scheme], tun,

@@ -6,9 +6,11 @@ back) are queued as they arrive.  Each call of Server.poll() retires the
 batches whose kernels have finished and admits queued requests, in arrival
 order, while their device memory fits the budget, into one new batch
 (dwt2d_batch_*: a few kernel launches for any mix of sizes, level counts,
-wavelets, storage types and directions).  Several batches may be in flight on
-the stream at once, so the host prepares the next batch while the GPU runs the
-previous one.
+wavelets, storage types and directions).  Several batches are in flight at
+once, each on its own stream of the executor's pool, so a batch admitted while
+others run starts on the device at once and its kernels share the SMs with
+theirs (the work of concurrently admitted requests overlaps), while the host
+prepares the next batch.
 
 Memory: a request reserves its output (kept resident on the device until the
 client calls release()), its share of the batch workspace, and a device copy of
@@ -108,9 +110,16 @@ def check_data(req: Request, t) -> str:
 
 
 class GpuExecutor:
-    """Runs a batch with the library's batched kernels on one stream."""
+    """Runs batches with the library's batched kernels on a pool of streams.
 
-    def __init__(self, device="cuda", scheme="nonsep_reduced", tuning=None, stream=None):
+    Batch k goes to stream k mod `streams`: the staging copies and the
+    allocations of the batch being formed use that stream too, so every batch
+    is ordered only after its own inputs, and batches on different streams run
+    concurrently.  `timing=True` records CUDA events (with timestamps) around
+    every batch, for measuring how they overlap."""
+
+    def __init__(self, device="cuda", scheme="nonsep_reduced", tuning=None, stream=None,
+                 streams: int = 4, timing: bool = False):
         from . import dwt2d as D
 
         self.D = D
@@ -119,14 +128,24 @@ class GpuExecutor:
             self.device = torch.device("cuda", torch.cuda.current_device())
         self.scheme = scheme
         self.tuning = tuning
-        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        if stream is not None:
+            self.streams = [stream]
+        else:
+            self.streams = [torch.cuda.Stream(self.device) for _ in range(max(1, int(streams)))]
+        self.timing = timing
+        self._next = 0
+
+    @property
+    def stream(self):
+        """The stream of the batch being formed."""
+        return self.streams[self._next]
 
     def workspace_bytes(self, req: Request) -> int:
         plan = self.D.Plan(req.height, req.width, req.levels, req.wavelet, self.scheme, req.dtype)
         return plan.workspace_bytes
 
     def empty(self, h, w, dtype):
-        with torch.cuda.stream(self.stream):  # blocks owned by the serving stream
+        with torch.cuda.stream(self.stream):  # blocks owned by the batch's stream
             return self.D.empty_image(h, w, dtype, self.device)
 
     def pitched(self, t: torch.Tensor) -> bool:
@@ -139,21 +158,31 @@ class GpuExecutor:
             dst.copy_(src, non_blocking=True)
 
     def launch(self, jobs):
+        st = self.stream
         batch = self.D.Batch(jobs, self.scheme, self.tuning)
-        with torch.cuda.stream(self.stream):
+        with torch.cuda.stream(st):
             ws = batch.workspace(self.device)
-        batch.upload(ws, stream=self.stream)
-        batch.launch(ws, stream=self.stream)
-        ev = torch.cuda.Event()
-        ev.record(self.stream)
-        return (batch, ws, ev)
+        batch.upload(ws, stream=st)
+        ev0 = None
+        if self.timing:
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev0.record(st)
+        batch.launch(ws, stream=st)
+        ev = torch.cuda.Event(enable_timing=self.timing)
+        ev.record(st)
+        self._next = (self._next + 1) % len(self.streams)
+        return (batch, ws, ev, st, ev0)
 
     def done(self, handle) -> bool:
         return handle[2].query()
 
     def status(self, handle) -> int:
-        batch, ws, _ = handle
-        return batch.status(ws, stream=self.stream)
+        batch, ws, _ev, st, _ev0 = handle
+        return batch.status(ws, stream=st)
+
+    def span(self, handle):
+        """(start, end) events of a batch launched with timing=True."""
+        return handle[4], handle[2]
 
 
 class Server:
@@ -180,6 +209,9 @@ class Server:
         self._loaders = cf.ThreadPoolExecutor(max_workers=loader_threads)
         self._loading = 0
         self.batches = 0
+        self.batch_sizes: List[int] = []  # requests per launched batch
+        self.retired_handles = []  # (handle, requests) of retired batches when keep_handles is set
+        self.keep_handles = False
 
     # ---- client side
     def submit(self, req: Request, t_arrival: Optional[float] = None) -> Ticket:
@@ -271,9 +303,12 @@ class Server:
                 return None
             return lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))]
 
+        sizes = self.batch_sizes
         return {"completed": c[DONE], "failed": c[FAILED], "cancelled": c[CANCELLED],
                 "rejected": c[REJECTED], "p50_s": q(0.50), "p99_s": q(0.99),
                 "max_s": lat[-1] if lat else None, "batches": self.batches,
+                "requests_per_batch": (sum(sizes) / len(sizes)) if sizes else None,
+                "max_batch_seen": max(sizes) if sizes else 0,
                 "peak_bytes": self.peak, "budget_bytes": self.budget}
 
     def reset_stats(self):
@@ -282,6 +317,7 @@ class Server:
             self.counts = {k: 0 for k in self.counts}
             self.latencies = []
             self.batches = 0
+            self.batch_sizes = []
             self.peak = self.in_use
 
     def close(self):
@@ -382,6 +418,7 @@ class Server:
                 self._finish(t, FAILED, f"launch failed: {e!r}")
             return
         self.batches += 1
+        self.batch_sizes.append(len(ok))
         self.inflight.append((handle, ok))
 
     def retire(self) -> int:
@@ -405,5 +442,7 @@ class Server:
                     self._unreserve(t, keep_out=True)  # the output stays resident
                     self._finish(t, DONE)
                 n += 1
+            if self.keep_handles:
+                self.retired_handles.append((handle, len(tickets)))
         self.inflight = still
         return n

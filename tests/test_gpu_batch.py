@@ -114,7 +114,7 @@ def test_mixed_batch_against_oracle():
                 assert np.array_equal(got.astype(np.int64), ref)
             else:
                 maxabs = float(np.max(np.abs(ref)))
-                assert float(np.max(np.abs(got - ref))) <= TOL_F32 * max(maxabs, 1.0) * lv
+                assert float(np.max(np.abs(got - ref))) <= TOL_F32 * max(maxabs, 1.0)
         else:
             assert_forward_matches(got, xh.numpy(), lv, wav, f"{tuple(xh.shape)} L{lv}")
 
@@ -250,3 +250,105 @@ def test_programmatic_batch_launch_changes_nothing():
         out[pdl] = (eager, [dst.cpu() for (_s, dst, _l, _w, _i) in jobs])
     for a, b in zip(out["0"][0] + out["0"][1], out["1"][0] + out["1"][1]):
         assert torch.equal(a, b)
+
+
+# ---- the persistent form: one launch per direction and storage type over a
+# queue of work items
+
+def _run_batch(jobs, scheme="nonsep_reduced", tuning=None):
+    batch = D.Batch(jobs, scheme, tuning)
+    ws = batch.workspace()
+    batch.upload(ws)
+    batch.launch(ws)
+    torch.cuda.synchronize()
+    assert batch.status(ws) == 0
+    return batch, ws
+
+
+@pytest.mark.parametrize("scheme", ["nonsep_reduced", "separable", "nonsep"])
+def test_persistent_batch_equals_single_image_calls(scheme):
+    jobs, _ = _jobs(MIXED, 2027, scheme)
+    batch, ws = _run_batch(jobs, scheme, {"persistent": 1})
+    launches, _ = batch.info()
+    # one persistent launch per (direction, storage type) present in the mix
+    kinds = {(inv, str(dt)) for (_h, _w, _l, _wv, dt, inv) in MIXED}
+    assert launches == len(kinds)
+    _assert_same_as_single(jobs, scheme, f"persistent {scheme}")
+
+
+def test_persistent_batch_graph_replay_on_new_inputs():
+    """The queue counters are reset by the launch itself: a captured graph
+    replays correctly, on new input contents, several times."""
+    jobs, _ = _jobs(MIXED, 31, "nonsep_reduced")
+    batch = D.Batch(jobs, "nonsep_reduced", {"persistent": 1})
+    ws = batch.workspace()
+    side = torch.cuda.Stream()
+    batch.upload(ws, stream=side)
+    side.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        batch.launch(ws, stream=side)
+    for rep, seed in enumerate((77, 78, 79)):
+        fresh, _ = _jobs(MIXED, seed)
+        for (src, dst, _l, _w, _i), (nsrc, _d, _l2, _w2, _i2) in zip(jobs, fresh):
+            src.copy_(nsrc)
+            dst.fill_(0)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert batch.status(ws) == 0, rep
+        _assert_same_as_single(jobs, "nonsep_reduced", f"graph replay {rep}")
+
+
+def _c4_spec(seed=2017, n=256):
+    """256 images, H, W ~ U{65..4096}, levels ~ U{1..6}, 75 % CDF 9/7 float32,
+    25 % LeGall 5/3 int32, forward (the batching workload)."""
+    rng = np.random.default_rng(seed)
+    spec = []
+    for _ in range(n):
+        h, w = int(rng.integers(65, 4097)), int(rng.integers(65, 4097))
+        lv = int(rng.integers(1, 7))
+        wav = "cdf97" if rng.random() < 0.75 else "legall53"
+        spec.append((h, w, lv, wav, torch.float32 if wav == "cdf97" else torch.int32, 0))
+    return spec
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_c4_batch_full_workload(persistent):
+    """The whole 256-image batching workload: every image bit for bit as the
+    single-image call, and sampled coefficients of every image against the
+    oracle (each from its dependency window)."""
+    spec = _c4_spec()
+    base = {"cdf97": synth.gradient_noise(4096, 4096, 2017),
+            "legall53": synth.uniform_int(4096, 4096, 2017)}
+    jobs, hosts = [], []
+    for (h, w, lv, wav, dt, inv) in spec:
+        xh = np.ascontiguousarray(base[wav][:h, :w])
+        src = D.empty_image(h, w, dt)
+        src.copy_(torch.from_numpy(xh))
+        jobs.append((src, D.empty_image(h, w, dt), lv, wav, 0))
+        hosts.append(xh)
+    _run_batch(jobs, "nonsep_reduced", {"persistent": persistent})
+    _assert_same_as_single(jobs, "nonsep_reduced", f"C4 persistent={persistent}")
+    if persistent == 0:
+        return  # the oracle samples once: the two forms gave the same bits
+    rng = np.random.default_rng(99)
+    for i, ((src, dst, lv, wav, _i), xh) in enumerate(zip(jobs, hosts)):
+        h, w = xh.shape
+        got = dst.cpu().numpy()
+        he, we = (h + 1) // 2, (w + 1) // 2
+        # two level-1 detail coefficients (small dependency windows), and every
+        # 16th image one coefficient of its coarsest level as well
+        pos = [(int(rng.integers(0, he)), int(rng.integers(we, w))),
+               (int(rng.integers(he, h)), int(rng.integers(0, w)))]
+        if i % 16 == 0:
+            sizes = L.level_sizes(h, w, lv)
+            hl, wl = sizes[-1]
+            pos.append((int(rng.integers(0, (hl + 1) // 2)), int(rng.integers(0, wl))))
+        maxabs = float(np.max(np.abs(xh)))
+        for r, c in pos:
+            ref = L.sample_coefficient(xh, lv, wav, r, c)
+            if wav == "legall53":
+                assert int(got[r, c]) == int(ref), (i, r, c)
+            else:
+                assert abs(float(got[r, c]) - float(ref)) <= TOL_F32 * maxabs, (i, r, c)

@@ -136,3 +136,78 @@ def test_poisson_stream_under_small_budget():
     assert st["peak_bytes"] <= budget
     assert st["p50_s"] > 0 and st["p99_s"] >= st["p50_s"]
     assert srv.in_use == 0
+
+
+def _batch_jobs(seed, n=48):
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for i in range(n):
+        h, w = int(rng.integers(100, 700)), int(rng.integers(100, 700))
+        wav, dt = ("cdf97", torch.float32) if i % 3 else ("legall53", torch.int32)
+        src = _data(h, w, wav, dt, seed * 100 + i)
+        jobs.append((src, D.empty_image(h, w, dt), int(rng.integers(1, 6)), wav, 0))
+    return jobs
+
+
+def _run_gated(ex, batches):
+    """Launch `batches` (job lists) through the executor, every stream held at
+    one gate that opens after all of them are queued: their device work
+    starts together whatever the host's launch latency.  Returns the handles
+    and the gate event."""
+    gate = torch.cuda.Event(enable_timing=True)
+    opener = torch.cuda.Stream()
+    with torch.cuda.stream(opener):
+        # the gate is recorded behind about 10 ms of spinning: every launch
+        # below is queued before it opens
+        torch.cuda._sleep(20_000_000)
+        gate.record(opener)
+    handles = []
+    for jobs in batches:
+        ex.stream.wait_event(gate)
+        handles.append(ex.launch(jobs))
+    torch.cuda.synchronize()
+    for h in handles:
+        assert ex.status(h) == 0
+    return handles, gate
+
+
+def test_batches_in_flight_overlap_on_the_device():
+    """Two batches admitted one after the other run on two streams of the
+    executor: on the device they overlap (the second starts before the first
+    ends, and together they take clearly less than the two alone), and each
+    gives the same bits as when it runs alone."""
+    jobs_a, jobs_b = _batch_jobs(1), _batch_jobs(2)
+    solo = []
+    outs_alone = []
+    for jobs in (jobs_a, jobs_b):
+        ex1 = S.GpuExecutor(streams=1, timing=True)
+        (h,), gate = _run_gated(ex1, [jobs])
+        e0, e1 = ex1.span(h)
+        solo.append(e0.elapsed_time(e1))
+        outs_alone.append([d.clone() for (_s, d, _l, _w, _i) in jobs])
+    ex2 = S.GpuExecutor(streams=2, timing=True)
+    (ha, hb), gate = _run_gated(ex2, [jobs_a, jobs_b])
+    assert ha[3] is not hb[3]  # two streams
+    a0, a1 = ex2.span(ha)
+    b0, b1 = ex2.span(hb)
+    t = lambda e: gate.elapsed_time(e)  # noqa: E731  ms after the gate opened
+    assert t(b0) < t(a1) and t(a0) < t(b1), (t(a0), t(a1), t(b0), t(b1))
+    together = max(t(a1), t(b1)) - min(t(a0), t(b0))
+    assert together < 0.85 * (solo[0] + solo[1]), (together, solo)
+    for jobs, ref in zip((jobs_a, jobs_b), outs_alone):
+        for (_s, d, _l, _w, _i), r in zip(jobs, ref):
+            assert torch.equal(d, r)
+
+
+def test_server_spreads_batches_over_streams():
+    """With several batches in flight, the server has them on different streams."""
+    ex = S.GpuExecutor(streams=3)
+    srv = S.Server(budget_bytes=4 << 30, executor=ex, max_batch=4, max_inflight=3)
+    srv.keep_handles = True
+    tickets = [srv.submit(_with_data(S.Request(700, 900, 4, "cdf97", torch.float32, False), 9 + i))
+               for i in range(12)]
+    assert srv.run_until_idle(60)
+    assert all(t.state == S.DONE for t in tickets)
+    streams = {id(h[3]) for h, _n in srv.retired_handles}
+    assert len(streams) == 3
+    assert srv.stats()["requests_per_batch"] == pytest.approx(4.0)
