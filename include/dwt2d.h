@@ -375,6 +375,20 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
                                 dwt2d_scheme scheme, const dwt2d_tuning* tuning,
                                 size_t* workspace_bytes);
 dwt2d_status dwt2d_batch_upload(dwt2d_batch_t batch, void* d_workspace, void* stream);
+
+/*
+ * dwt2d_batch_staging_bytes -- host bytes of the batch's descriptor tables.
+ * dwt2d_batch_upload_staged -- dwt2d_batch_upload, copying the tables from
+ *   h_staging: pinned host memory (cudaHostAlloc or registered), 16-byte
+ *   aligned, at least dwt2d_batch_staging_bytes long, owned by the caller and
+ *   left untouched until the stream has passed the upload.  A copy from
+ *   pageable memory may make the host wait until the stream drains; from
+ *   pinned memory it is queued at once, so a serving loop can queue a new
+ *   batch on another stream while earlier batches run.
+ */
+dwt2d_status dwt2d_batch_staging_bytes(dwt2d_batch_t batch, size_t* bytes);
+dwt2d_status dwt2d_batch_upload_staged(dwt2d_batch_t batch, void* d_workspace, void* h_staging,
+                                       size_t staging_bytes, void* stream);
 dwt2d_status dwt2d_batch_launch(dwt2d_batch_t batch, void* d_workspace, void* stream);
 dwt2d_status dwt2d_batch_info(dwt2d_batch_t batch, int32_t* launches, int64_t* warps);
 void dwt2d_batch_destroy(dwt2d_batch_t batch);

@@ -1397,7 +1397,31 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
     return DWT2D_OK;
 }
 
+static dwt2d_status batch_upload(dwt2d_batch_t b, void* d_ws, void* h_staging, size_t staging_bytes,
+                                 void* stream);
+
 dwt2d_status dwt2d_batch_upload(dwt2d_batch_t b, void* d_ws, void* stream) {
+    return batch_upload(b, d_ws, nullptr, 0, stream);
+}
+
+dwt2d_status dwt2d_batch_staging_bytes(dwt2d_batch_t b, size_t* bytes) {
+    if (!b || !bytes) return DWT2D_ERR_INVALID;
+    *bytes = (b->refs.size() + b->qorder.size()) * sizeof(BatchEntry);
+    return DWT2D_OK;
+}
+
+dwt2d_status dwt2d_batch_upload_staged(dwt2d_batch_t b, void* d_ws, void* h_staging, size_t bytes,
+                                       void* stream) {
+    if (!b || !h_staging) return DWT2D_ERR_INVALID;
+    size_t need = 0;
+    dwt2d_batch_staging_bytes(b, &need);
+    if (bytes < need || ((uintptr_t)h_staging & 15u)) return DWT2D_ERR_INVALID;
+    return batch_upload(b, d_ws, h_staging, bytes, stream);
+}
+
+static dwt2d_status batch_upload(dwt2d_batch_t b, void* d_ws, void* h_staging, size_t staging_bytes,
+                                 void* stream) {
+    (void)staging_bytes;
     if (!b || !d_ws) return DWT2D_ERR_INVALID;
     if (!aligned16(d_ws) || ((uintptr_t)d_ws & 255u)) return DWT2D_ERR_ALIGN;
     cudaStream_t st = as_stream(stream);
@@ -1428,10 +1452,19 @@ dwt2d_status dwt2d_batch_upload(dwt2d_batch_t b, void* d_ws, void* stream) {
                                     : launch_inv_batched(L.elem_kind, sch, L.nl, nullptr, 0, 0, st, false);
         if (e != cudaSuccess) return DWT2D_ERR_CUDA;
     }
-    if (!b->table.empty() &&
-        cudaMemcpyAsync(wsb + b->table_off, b->table.data(), b->table.size() * sizeof(BatchEntry),
-                        cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return DWT2D_ERR_CUDA;
+    // the tables go up from the caller's pinned staging buffer when given one
+    // (a copy from pageable memory may wait for the stream to drain)
+    auto upload = [&](size_t dev_off, const std::vector<BatchEntry>& v, size_t stage_off) {
+        if (v.empty()) return cudaSuccess;
+        const size_t bytes = v.size() * sizeof(BatchEntry);
+        const void* srcp = v.data();
+        if (h_staging) {
+            memcpy(static_cast<char*>(h_staging) + stage_off, v.data(), bytes);
+            srcp = static_cast<char*>(h_staging) + stage_off;
+        }
+        return cudaMemcpyAsync(wsb + dev_off, srcp, bytes, cudaMemcpyHostToDevice, st);
+    };
+    if (upload(b->table_off, b->table, 0) != cudaSuccess) return DWT2D_ERR_CUDA;
     // queue mode: the same entries queue by queue, numbered within their
     // queue, with their done counters and the group each depends on
     b->qtable.clear();
@@ -1465,9 +1498,7 @@ dwt2d_status dwt2d_batch_upload(dwt2d_batch_t b, void* d_ws, void* stream) {
                                                        nullptr, 0, st);
         if (e != cudaSuccess) return DWT2D_ERR_CUDA;
     }
-    if (!b->qtable.empty() &&
-        cudaMemcpyAsync(wsb + b->qtable_off, b->qtable.data(), b->qtable.size() * sizeof(BatchEntry),
-                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (upload(b->qtable_off, b->qtable, b->table.size() * sizeof(BatchEntry)) != cudaSuccess)
         return DWT2D_ERR_CUDA;
     if (cudaMemsetAsync(d_ws, 0, sizeof(int), st) != cudaSuccess) return DWT2D_ERR_CUDA;
     return DWT2D_OK;

@@ -111,6 +111,10 @@ def lib() -> ctypes.CDLL:
     L.dwt2d_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(BatchItem), i32, ctypes.c_int,
                                      ctypes.POINTER(Tuning), ctypes.POINTER(sz)]
     L.dwt2d_batch_upload.argtypes = [vp, vp, vp]
+    L.dwt2d_batch_staging_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+    L.dwt2d_batch_staging_bytes.restype = ctypes.c_int
+    L.dwt2d_batch_upload_staged.argtypes = [vp, vp, vp, sz, vp]
+    L.dwt2d_batch_upload_staged.restype = ctypes.c_int
     L.dwt2d_batch_launch.argtypes = [vp, vp, vp]
     L.dwt2d_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
     L.dwt2d_batch_destroy.argtypes = [vp]
@@ -327,7 +331,22 @@ class Batch:
         # 256-byte aligned (the caching allocator's blocks are)
         return torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=device)
 
-    def upload(self, workspace: torch.Tensor, stream=None):
+    def staging_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().dwt2d_batch_staging_bytes(self._h, ctypes.byref(n)), "batch_staging_bytes")
+        return n.value
+
+    def upload(self, workspace: torch.Tensor, stream=None, staging: Optional[torch.Tensor] = None):
+        """Write the descriptor tables into the workspace.  With `staging` (a
+        pinned uint8 host tensor of at least staging_bytes(), kept alive until
+        the stream has passed the upload) the copy is queued without waiting
+        for the stream."""
+        if staging is not None:
+            _check(lib().dwt2d_batch_upload_staged(self._h, ctypes.c_void_p(workspace.data_ptr()),
+                                                   ctypes.c_void_p(staging.data_ptr()),
+                                                   staging.numel() * staging.element_size(),
+                                                   _stream_ptr(stream)), "dwt2d_batch_upload_staged")
+            return
         _check(lib().dwt2d_batch_upload(self._h, ctypes.c_void_p(workspace.data_ptr()),
                                         _stream_ptr(stream)), "dwt2d_batch_upload")
 

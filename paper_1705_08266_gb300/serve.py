@@ -134,6 +134,7 @@ class GpuExecutor:
             self.streams = [torch.cuda.Stream(self.device) for _ in range(max(1, int(streams)))]
         self.timing = timing
         self._next = 0
+        self._ws_cache = {}
 
     @property
     def stream(self):
@@ -141,8 +142,16 @@ class GpuExecutor:
         return self.streams[self._next]
 
     def workspace_bytes(self, req: Request) -> int:
-        plan = self.D.Plan(req.height, req.width, req.levels, req.wavelet, self.scheme, req.dtype)
-        return plan.workspace_bytes
+        # one plan per distinct transform description (admission runs per request)
+        key = (req.height, req.width, req.levels, req.wavelet, req.dtype)
+        n = self._ws_cache.get(key)
+        if n is None:
+            plan = self.D.Plan(req.height, req.width, req.levels, req.wavelet, self.scheme, req.dtype)
+            n = plan.workspace_bytes
+            if len(self._ws_cache) > 65536:
+                self._ws_cache.clear()
+            self._ws_cache[key] = n
+        return n
 
     def empty(self, h, w, dtype):
         with torch.cuda.stream(self.stream):  # blocks owned by the batch's stream
@@ -162,7 +171,11 @@ class GpuExecutor:
         batch = self.D.Batch(jobs, self.scheme, self.tuning)
         with torch.cuda.stream(st):
             ws = batch.workspace(self.device)
-        batch.upload(ws, stream=st)
+        # pinned staging: queuing the table copy does not wait for the stream,
+        # so this batch is queued while earlier ones still run; the handle
+        # keeps the staging alive until the batch retires
+        staging = torch.empty(max(batch.staging_bytes(), 16), dtype=torch.uint8, pin_memory=True)
+        batch.upload(ws, stream=st, staging=staging)
         ev0 = None
         if self.timing:
             ev0 = torch.cuda.Event(enable_timing=True)
@@ -171,13 +184,13 @@ class GpuExecutor:
         ev = torch.cuda.Event(enable_timing=self.timing)
         ev.record(st)
         self._next = (self._next + 1) % len(self.streams)
-        return (batch, ws, ev, st, ev0)
+        return (batch, ws, ev, st, ev0, staging)
 
     def done(self, handle) -> bool:
         return handle[2].query()
 
     def status(self, handle) -> int:
-        batch, ws, _ev, st, _ev0 = handle
+        batch, ws, _ev, st = handle[:4]
         return batch.status(ws, stream=st)
 
     def span(self, handle):
