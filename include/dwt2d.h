@@ -134,7 +134,8 @@ typedef struct {
                                       large_segment rows long at this many warps per SM take it
                                       (default 48 for CDF 9/7, 44 for LeGall 5/3 at 2 columns per
                                       lane, 24 at 4; -1: never) */
-    int32_t inv_warps_per_sm_large;/* the same for the inverse (default 64; -1: never) */
+    int32_t inv_warps_per_sm_large;/* the same for the inverse (default 64 at 2 columns per lane,
+                                      24 at 4; -1: never) */
     int32_t large_segment;         /* that threshold, quadruple rows of the launch's last level
                                       (default 16) */
     int32_t min_segment;           /* shortest row segment of a warp (default 2) */
@@ -145,7 +146,7 @@ typedef struct {
     int32_t fwd_cols_per_lane;     /* quadruple columns per lane, 2 or 4 (default: 4 for a float
                                       launch of at most 2 fused levels whose rows give long
                                       segments at 24 warps per SM, else 2) */
-    int32_t inv_cols_per_lane;     /* the same for the inverse (default 2) */
+    int32_t inv_cols_per_lane;     /* the same for the inverse, 2 or 4 (default 2) */
     int32_t programmatic_launch;   /* device entry points launch with programmatic stream
                                       serialization (default on) */
     int32_t host_bands;            /* row bands of the *_host entry points, 1-64 (default 8) */
@@ -228,11 +229,12 @@ dwt2d_status dwt2d_inverse_host(dwt2d_plan_t plan, const void* h_src, int64_t h_
                                 float scale, void* stream);
 
 /*
- * dwt2d_workspace_init -- zero the status word of a workspace (asynchronous on
- *   stream).  Call once after allocating a workspace.
+ * dwt2d_workspace_init -- zero the 256-byte header of a workspace (its first
+ *   word is the status word; asynchronous on stream).  Call once after
+ *   allocating a workspace.
  * dwt2d_workspace_status -- copy the status word to the host (synchronizes
- *   stream), reset it to zero, and return DWT2D_OK or the recorded error
- *   (DWT2D_ERR_TIMEOUT).
+ *   stream) and return DWT2D_OK or the recorded error (DWT2D_ERR_TIMEOUT);
+ *   after an error it zeroes the header again.
  */
 dwt2d_status dwt2d_workspace_init(void* d_workspace, void* stream);
 dwt2d_status dwt2d_workspace_status(void* d_workspace, void* stream);

@@ -44,6 +44,7 @@ struct dwt2d_plan_s {
     int inv_warps_large;  // the same rule for inverse launches
     int fwd_q1;  // quadruple columns per lane of the forward kernel (2 or 4; 0: automatic)
     int fwd_warps_large4, fwd_short4;  // the large-launch rule at 4 columns per lane
+    int inv_warps_large4;
     int inv_q1;  // the same for the inverse
     int min_segq;
     int pdl;  // device entry points: launches with programmatic stream serialization
@@ -237,7 +238,7 @@ dwt2d_status check_buffers(const dwt2d_plan_s* p, const void* src, int64_t sp, c
 // Warps of a streaming kernel resident per SM (their register budgets).
 int resident_per_sm(bool fwd, int nl, int q1, int scheme) {
     if (fwd) return q1 <= 2 ? 16 : (nl <= 2 ? 12 : 8);
-    return q1 <= 2 ? (scheme == SCH_NONSEP ? 12 : 16) : 8;
+    return q1 <= 2 ? (scheme == SCH_NONSEP ? 12 : 16) : 12;
 }
 
 // Warp work decomposition of one streaming launch.
@@ -418,30 +419,35 @@ dwt2d_status build_group(const dwt2d_plan_s* p, bool fwd, int k, const void* src
     a.out_elems = last ? (long long)p->H * dst_pe : belems[k & 1];
     out->nl = g.n;
     if (g.n <= 2) {
-        // TMA ring: boxes of the Mallat array and of the LL source
-        const int q1 = p->inv_q1;
+        // TMA ring: boxes of the Mallat array and of the LL source.  2 columns
+        // per lane unless 4 are asked for (measured: 4 is 7 % slower for the
+        // 8192^2 finest launch, 5 % faster at 16384^2 float32)
+        const int rows = (a.lv[0].h + 1) / 2;
+        const int q1 = p->inv_q1 == 4 ? 4 : 2;
         const int al = 16 / p->elem;  // boxes start at a 16-byte boundary
         const int w1 = 32 * q1 + al, w2 = 16 * q1 + al;
+        const int sr = inv_slot_rows(q1);  // level-1 box rows; level-2 boxes sr / 2
         dwt2d_status s = plan_only ? DWT2D_OK
-                                   : make_map(&out->m[0], src, p->H, p->W, src_pe, p->elem, elem_kind, w1, 4);
+                                   : make_map(&out->m[0], src, p->H, p->W, src_pe, p->elem, elem_kind, w1, sr);
         if (s == DWT2D_OK && !plan_only)
-            s = make_map(&out->m[1], src, p->H, p->W, src_pe, p->elem, elem_kind, w2, 2);
+            s = make_map(&out->m[1], src, p->H, p->W, src_pe, p->elem, elem_kind, w2, sr / 2);
         const int llh = (a.lv[g.n - 1].h + 1) / 2, llw = (a.lv[g.n - 1].w + 1) / 2;
         const bool ll_is_src = k == 0;
         if (s == DWT2D_OK && !plan_only)
             s = make_map(&out->m[2], ll_in, ll_is_src ? p->H : llh, ll_is_src ? p->W : llw, ll_pitch,
-                         p->elem, elem_kind, g.n == 1 ? w1 : w2, g.n == 1 ? 4 : 2);
+                         p->elem, elem_kind, g.n == 1 ? w1 : w2, g.n == 1 ? sr : sr / 2);
         if (s != DWT2D_OK) return s;
         const int res = resident_per_sm(false, g.n, q1, sch);
+        const int large = q1 == 4 ? p->inv_warps_large4 : p->inv_warps_large;
         const int sd = uniform_segments ? 0 : p->inv_short;
         // the inverse measured fastest with its segments top to bottom
-        decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, q1, inv_target, &a, &out->grid,
-                  kInvTmaWarps, segq_fixed, res, 0, p->inv_seg_f);
-        if (segq_fixed <= 0 && p->inv_warps_large > inv_target) {
+        decompose(p, a.lv[0].w, rows, g.n, rho, q1, inv_target, &a, &out->grid, kInvTmaWarps,
+                  segq_fixed, res, 0, p->inv_seg_f);
+        if (segq_fixed <= 0 && large > inv_target) {
             FusedArgs b = a;
             int grid_b = 0;
-            decompose(p, a.lv[0].w, (a.lv[0].h + 1) / 2, g.n, rho, q1, p->inv_warps_large, &b, &grid_b,
-                      kInvTmaWarps, 0, res, sd, p->inv_seg_f);
+            decompose(p, a.lv[0].w, rows, g.n, rho, q1, large, &b, &grid_b, kInvTmaWarps, 0, res, sd,
+                      p->inv_seg_f);
             if (b.segq >= p->large_segq) {
                 a = b;
                 out->grid = grid_b;
@@ -775,7 +781,9 @@ static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width
     p->inv_short = o.inv_short_tail < 0 ? 0 : opt(o.inv_short_tail, 4);
     p->host_bands = opt(o.host_bands, 8);
     p->host_pipeline = opt(o.host_pipeline, 1) > 0;
-    p->inv_q1 = o.inv_cols_per_lane == 4 && !half ? 4 : 2;
+    p->inv_q1 = o.inv_cols_per_lane == 4 ? 4 : 2;
+    const int iwl4 = opt(o.inv_warps_per_sm_large, 24);
+    p->inv_warps_large4 = (tuning && tuning->warps_per_sm > 0) || iwl4 < 0 ? 0 : sms * iwl4;
 
     // workspace: header | LL buffer A | LL buffer B | (multipass) X | Y
     size_t off = kHeader;
@@ -1093,18 +1101,18 @@ static dwt2d_status run_host_inv_pipelined(dwt2d_plan_s* p, const void* h_src, i
     FusedArgs base = gf.a;
     base.seg_f = 1;
     const int lag = p->wavelet == DWT2D_CDF97 ? 2 : 1;
-    const int pro_slots = n0 == 2 ? lag : 0;
     const int ne_r2 = n0 == 2 ? (p->hs[1] + 1) / 2 : 0;
+    const int sr = inv_slot_rows(gf.q1), spro = n0 == 2 ? 2 * lag / (sr / 2) : 0;
     auto ready = [&](int seg, int c) {  // rows segment `seg` reads are all in after band c
         if (c == B - 1) return true;
         const int A0 = seg * base.segq, A1 = std::min(A0 + base.segq, ne_r1);
-        const int qstart = std::max(A0 - lag, 0) & ~3;
-        const int nmain = (A1 + lag - qstart + 3) / 4;
-        const int end1 = std::min(qstart + 4 * nmain, ne_r1);
+        const int qstart = std::max(A0 - lag, 0) & ~(sr - 1);
+        const int nmain = (A1 + lag - qstart + sr - 1) / sr;
+        const int end1 = std::min(qstart + sr * nmain, ne_r1);
         if (end1 > std::min((c + 1) * rb, ne_r1)) return false;
         if (n0 == 2) {
-            const int qlast = qstart - 4 * pro_slots + 4 * (nmain + pro_slots - 1);
-            const int end2 = std::min(qlast / 2 + lag + 2, ne_r2);
+            const int qlast = qstart - sr * spro + sr * (nmain + spro - 1);
+            const int end2 = std::min(qlast / 2 + lag + sr / 2, ne_r2);
             if (end2 > std::min(((c + 1) * rb) >> 1, ne_r2)) return false;
         }
         return true;
@@ -1150,7 +1158,7 @@ static dwt2d_status run_host(dwt2d_plan_t p, bool fwd, const void* h_src, int64_
         return run_host_fwd_pipelined(p, h_src, hsp, h_dst, hdp, d_in, d_out, dpitch, d_ws, st);
     if (!fwd && p->H >= 1024 && !multipass(p->scheme) && p->host_pipeline &&
         check_buffers(p, d_in, dpitch, d_out, dpitch, d_ws) == DWT2D_OK && p->groups[0].n <= 2 &&
-        p->inv_q1 == 2 && scale_ok(p, scale) && host_resources(p))
+        scale_ok(p, scale) && host_resources(p))
         return run_host_inv_pipelined(p, h_src, hsp, h_dst, hdp, d_in, d_out, dpitch, d_ws, st);
     // one linear copy when both sides are unpadded (faster than a 2-D copy)
     auto copy = [&](void* dst, int64_t dp, const void* src, int64_t sp, cudaMemcpyKind kind) {
@@ -1181,8 +1189,9 @@ dwt2d_status dwt2d_inverse_host(dwt2d_plan_t p, const void* h_src, int64_t hsp, 
 dwt2d_status dwt2d_workspace_init(void* d_ws, void* stream) {
     if (!d_ws) return DWT2D_ERR_INVALID;
     if (!aligned16(d_ws)) return DWT2D_ERR_ALIGN;
-    return cudaMemsetAsync(d_ws, 0, sizeof(int), as_stream(stream)) == cudaSuccess ? DWT2D_OK
-                                                                                   : DWT2D_ERR_CUDA;
+    // the whole header (its first word is the status word)
+    return cudaMemsetAsync(d_ws, 0, kHeader, as_stream(stream)) == cudaSuccess ? DWT2D_OK
+                                                                               : DWT2D_ERR_CUDA;
 }
 
 dwt2d_status dwt2d_workspace_status(void* d_ws, void* stream) {
@@ -1193,7 +1202,8 @@ dwt2d_status dwt2d_workspace_status(void* d_ws, void* stream) {
         return DWT2D_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return DWT2D_ERR_CUDA;
     if (h != 0) {
-        if (cudaMemsetAsync(d_ws, 0, sizeof(int), st) != cudaSuccess) return DWT2D_ERR_CUDA;
+        // clear the header for the next call
+        if (cudaMemsetAsync(d_ws, 0, kHeader, st) != cudaSuccess) return DWT2D_ERR_CUDA;
         return (dwt2d_status)h;
     }
     return DWT2D_OK;

@@ -773,21 +773,27 @@ struct Pipe<float, Q, SCH_RED, true> {
     using type = Chain<float, Q, OpFT<0, 1, true, P>, OpFS<1, 1, true, P>, OpFT<2, 1, true, P>,
                        OpFS<3, 1, true, P>>;
 };
-// CDF 9/7 inverse: undo every step in reverse order.
+// CDF 9/7 inverse: undo every step in reverse order (packed; strided pairs
+// at 4 columns per lane).
+template <int Q>
+constexpr int inv_pk() { return Q >= 4 ? 2 : 1; }
 template <int Q>
 struct Pipe<float, Q, SCH_SEP, false> {
-    using type = Chain<float, Q, OpFSV<3, -1, 1>, OpFSH<3, -1, 1>, OpFTV<2, -1, 1>, OpFTH<2, -1, 1>,
-                       OpFSV<1, -1, 1>, OpFSH<1, -1, 1>, OpFTV<0, -1, 1>, OpFTH<0, -1, 1>>;
+    static constexpr int P = inv_pk<Q>();
+    using type = Chain<float, Q, OpFSV<3, -1, P>, OpFSH<3, -1, P>, OpFTV<2, -1, P>, OpFTH<2, -1, P>,
+                       OpFSV<1, -1, P>, OpFSH<1, -1, P>, OpFTV<0, -1, P>, OpFTH<0, -1, P>>;
 };
 template <int Q>
 struct Pipe<float, Q, SCH_NONSEP, false> {
-    using type = Chain<float, Q, OpFS<3, -1, false, 1>, OpFT<2, -1, false, 1>,
-                       OpFS<1, -1, false, 1>, OpFT<0, -1, false, 1>>;
+    static constexpr int P = inv_pk<Q>();
+    using type = Chain<float, Q, OpFS<3, -1, false, P>, OpFT<2, -1, false, P>,
+                       OpFS<1, -1, false, P>, OpFT<0, -1, false, P>>;
 };
 template <int Q>
 struct Pipe<float, Q, SCH_RED, false> {
-    using type = Chain<float, Q, OpFS<3, -1, true, 1>, OpFT<2, -1, true, 1>,
-                       OpFS<1, -1, true, 1>, OpFT<0, -1, true, 1>>;
+    static constexpr int P = inv_pk<Q>();
+    using type = Chain<float, Q, OpFS<3, -1, true, P>, OpFT<2, -1, true, P>,
+                       OpFS<1, -1, true, P>, OpFT<0, -1, true, P>>;
 };
 // LeGall 5/3 (reversible): the reduced scheme keeps the floors on whole 1-D
 // sums and is therefore the same integer dataflow as the non-separable one.

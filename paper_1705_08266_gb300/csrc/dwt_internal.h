@@ -46,6 +46,7 @@ struct FusedArgs {
     int pdl;                         // host: launch with programmatic stream serialization
 };
 
+
 // Where a multipass kernel reads or writes a level's coefficients.
 struct Layout {
     const void* p;       // kind 0: interleaved image layout; kind 1: Mallat array (details)
@@ -142,6 +143,8 @@ cudaError_t launch_inv_tma(int elem, int scheme, int nl, int q1, const CUtensorM
                            const CUtensorMap& m2, const CUtensorMap& ml, const FusedArgs& a,
                            int grid, cudaStream_t st);
 size_t inv_tma_smem_bytes(int elem_bytes, int nl, int q1);
+// Level-1 quadruple rows per slot of the TMA inverse: 4, or 2 with 4 columns per lane.
+int inv_slot_rows(int q1);
 constexpr int kInvTmaWarps = 1;  // one-warp CTAs, as the forward
 
 // One level of the separable convolution scheme (Sec. 2, Eq. 1).

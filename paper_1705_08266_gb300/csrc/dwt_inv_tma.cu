@@ -20,21 +20,28 @@ namespace dwt {
 constexpr int kInvWarps = kInvTmaWarps;  // warps per CTA (independent)
 constexpr int kInvSlots = 3;  // ring depth per warp
 
+// Level-1 quadruple rows per slot: 4, or 2 with 4 columns per lane (the same
+// 8 quadruples per lane per lifting step as 2 columns in 4 rows).
+template <int Q1>
+__host__ __device__ constexpr int inv_slot_quads() { return Q1 >= 4 ? 2 : 4; }
+
 // Box widths carry A extra elements (16 bytes) so a box can start at the
 // column rounded down to 16 bytes.
 template <class S, int NL, int Q1>
 struct InvLayout {
+    static constexpr int SR = inv_slot_quads<Q1>();  // level-1 rows per slot
+    static constexpr int SR2 = SR / 2;               // level-2 rows per slot
     static constexpr int A = 16 / (int)sizeof(S);
     static constexpr int Q2 = Q1 / 2;
     static constexpr int W1 = 32 * Q1 + A;     // level-1 box width (elements)
     static constexpr int W2 = 32 * Q2 + A;     // level-2 box width
     static constexpr int E128 = 128 / (int)sizeof(S);
-    static constexpr int R1 = (4 * W1 + E128 - 1) / E128 * E128;  // one level-1 box region, 128-B multiple
-    static constexpr int R2 = (2 * W2 + E128 - 1) / E128 * E128;  // one level-2 box region
+    static constexpr int R1 = (SR * W1 + E128 - 1) / E128 * E128;   // one level-1 box region, 128-B multiple
+    static constexpr int R2 = (SR2 * W2 + E128 - 1) / E128 * E128;  // one level-2 box region
     // NL == 1: LL1 HL1 LH1 HH1; NL == 2: HL1 LH1 HH1, LL2 HL2 LH2 HH2
     static constexpr int SLOT = NL == 1 ? 4 * R1 : 3 * R1 + 4 * R2;
-    static constexpr uint32_t BYTES1 = 4 * W1 * sizeof(S);  // bytes one level-1 box brings
-    static constexpr uint32_t BYTES2 = 2 * W2 * sizeof(S);
+    static constexpr uint32_t BYTES1 = SR * W1 * sizeof(S);  // bytes one level-1 box brings
+    static constexpr uint32_t BYTES2 = SR2 * W2 * sizeof(S);
 };
 
 // Lane's Q values of one band row held in shared memory at p (+ lane * Q).
@@ -62,25 +69,28 @@ struct InvWarpT {
     bool lane_ok, vec_out;
     bool vec_row;   // this lane's 2 Q1 output columns are one aligned vector inside the row
 
+    static constexpr int SR = Lay::SR;
+    static constexpr int SR2 = Lay::SR2;
+
     template <bool EDGE>
     __device__ __forceinline__ void slot(const S* sm, int q0, bool level1) {
-        Block<T, Q1, 4> b1;
+        Block<T, Q1, SR> b1;
         if constexpr (NL == 2) {
             constexpr int QQ = Q2;
-            Block<T, QQ, 2> b2;
+            Block<T, QQ, SR2> b2;
             const S* base2 = sm + 3 * Lay::R1;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < SR2; ++k) {
                 lds_cols<S, T, QQ>(b2.r[k].c[0], base2 + 0 * Lay::R2 + k * Lay::W2 + o2l + QQ * lane);
                 lds_cols<S, T, QQ>(b2.r[k].c[1], base2 + 1 * Lay::R2 + k * Lay::W2 + o2h + QQ * lane);
                 lds_cols<S, T, QQ>(b2.r[k].c[2], base2 + 2 * Lay::R2 + k * Lay::W2 + o2l + QQ * lane);
                 lds_cols<S, T, QQ>(b2.r[k].c[3], base2 + 3 * Lay::R2 + k * Lay::W2 + o2h + QQ * lane);
             }
-            e2.template push<EDGE, 2>(b2, q0 / 2 + LAG, x2);
+            e2.template push<EDGE, SR2>(b2, q0 / 2 + LAG, x2);
             if (!level1) return;
-            // level-2 rows q0/2, q0/2 + 1 -> LL rows q0 .. q0 + 3 of level 1
+            // level-2 rows q0/2 .. q0/2 + SR2 - 1 -> LL rows q0 .. q0 + SR - 1 of level 1
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < SR2; ++k) {
 #pragma unroll
                 for (int j = 0; j < QQ; ++j) {
                     b1.r[2 * k].c[0][2 * j] = b2.r[k].c[0][j];
@@ -90,42 +100,54 @@ struct InvWarpT {
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < SR; ++k) {
                 lds_cols<S, T, Q1>(b1.r[k].c[1], sm + 0 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
                 lds_cols<S, T, Q1>(b1.r[k].c[2], sm + 1 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
                 lds_cols<S, T, Q1>(b1.r[k].c[3], sm + 2 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < SR; ++k) {
                 lds_cols<S, T, Q1>(b1.r[k].c[0], sm + 0 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
                 lds_cols<S, T, Q1>(b1.r[k].c[1], sm + 1 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
                 lds_cols<S, T, Q1>(b1.r[k].c[2], sm + 2 * Lay::R1 + k * Lay::W1 + o1l + Q1 * lane);
                 lds_cols<S, T, Q1>(b1.r[k].c[3], sm + 3 * Lay::R1 + k * Lay::W1 + o1h + Q1 * lane);
             }
         }
-        e1.template push<EDGE, 4>(b1, q0, x1);
+        e1.template push<EDGE, SR>(b1, q0, x1);
         const int r1 = q0 - LAG;
         // quadruple row r -> output rows 2r (c0 c1 interleaved) and 2r + 1
         // (c2 c3); one row address per slot, advanced by the pitch
         S* p = out + (long long)(2 * r1) * opitch + x0l;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < SR; ++k) {
             const int r = r1 + k;
-            if (lane_ok && r >= A0 && r < A1) {
-                T ev[2 * Q1], od[2 * Q1];
+            const bool ok = lane_ok && r >= A0 && r < A1;
+            T ev[2 * Q1], od[2 * Q1];
 #pragma unroll
-                for (int j = 0; j < Q1; ++j) {
-                    ev[2 * j] = b1.r[k].c[0][j];
-                    ev[2 * j + 1] = b1.r[k].c[1][j];
-                    od[2 * j] = b1.r[k].c[2][j];
-                    od[2 * j + 1] = b1.r[k].c[3][j];
-                }
+            for (int j = 0; j < Q1; ++j) {
+                ev[2 * j] = b1.r[k].c[0][j];
+                ev[2 * j + 1] = b1.r[k].c[1][j];
+                od[2 * j] = b1.r[k].c[2][j];
+                od[2 * j + 1] = b1.r[k].c[3][j];
+            }
+            if constexpr (!EDGE) {
+                // border-free slot: whole vectors inside the image, one predicate
+                store_fast_px(ev, p, ok);
+                store_fast_px(od, p + opitch, ok);
+            } else if (ok) {
                 store_px(ev, 2 * r, p);
                 store_px(od, 2 * r + 1, p + opitch);
             }
             p += 2 * opitch;
         }
+    }
+
+    __device__ __forceinline__ void store_fast_px(const T (&v)[2 * Q1], S* p, bool ok) {
+        S w[2 * Q1];
+#pragma unroll
+        for (int j = 0; j < 2 * Q1; ++j) w[j] = Storage<S>::st(v[j]);
+        if (ok && store_ok(p, 2 * Q1 * (int)sizeof(S))) st_vec<S, 2 * Q1>(p, w);
     }
 
     // Output row y at p (= out + y * opitch + x0l).
@@ -146,12 +168,12 @@ struct InvWarpT {
     }
 };
 
-__device__ __forceinline__ bool inv_rows_interior(int q0, int nl, int lag, const int* no_r) {
-    // level 1: rows [q0, q0 + 3]; level 2: rows [q0/2 + lag, q0/2 + lag + 1]
-    if (q0 - lag - 1 < 0 || q0 + 4 >= no_r[0]) return false;
+__device__ __forceinline__ bool inv_rows_interior(int q0, int sr, int nl, int lag, const int* no_r) {
+    // level 1: rows [q0, q0 + sr - 1]; level 2: rows [q0/2 + lag, q0/2 + lag + sr/2 - 1]
+    if (q0 - lag - 1 < 0 || q0 + sr >= no_r[0]) return false;
     if (nl >= 2) {
         const int lo = q0 / 2 + lag;
-        if (lo - lag - 1 < 0 || lo + 2 >= no_r[1]) return false;
+        if (lo - lag - 1 < 0 || lo + sr / 2 >= no_r[1]) return false;
     }
     return true;
 }
@@ -165,8 +187,9 @@ __device__ __forceinline__ bool inv_body(const CUtensorMap* m1p, const CUtensorM
     using Lay = InvLayout<S, NL, Q1>;
     constexpr int LAG = W::LAG;
     constexpr int RHO = LAG;
+    constexpr int SR = Lay::SR;
     constexpr int PRO = NL == 2 ? 2 * LAG : 0;  // level-2 rows pushed ahead (LAG + RHO)
-    constexpr int PRO_SLOTS = PRO / 2;           // slots that feed level 2 only
+    constexpr int PRO_SLOTS = PRO / (SR / 2);    // slots that feed level 2 only
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -215,14 +238,15 @@ __device__ __forceinline__ bool inv_body(const CUtensorMap* m1p, const CUtensorM
         w.o2l = xl2 - bx2l;
         hfast = hfast && g2w >= 2 && g2w + 32 * W::Q2 + 2 <= (a.lv[1].w >> 1);
     }
+    hfast = hfast && w.vec_out;  // the border-free code stores whole vectors
     w.e1.init();
     if constexpr (NL >= 2) w.e2.init();
 
     // level-1 input rows of this item: outputs [A0, A1) need [A0 - RHO, A1 - 1 + LAG]
-    const int qstart = max(w.A0 - RHO, 0) & ~3;
-    const int nmain = (w.A1 + LAG - qstart + 3) / 4;
+    const int qstart = max(w.A0 - RHO, 0) & ~(SR - 1);
+    const int nmain = (w.A1 + LAG - qstart + SR - 1) / SR;
     const int nslots = nmain + PRO_SLOTS;
-    const int qbase = qstart - 4 * PRO_SLOTS;
+    const int qbase = qstart - SR * PRO_SLOTS;
 
     const uint32_t ring_s = smem_u32(ring);
     const uint32_t bar_s = smem_u32(bars);
@@ -230,7 +254,7 @@ __device__ __forceinline__ bool inv_body(const CUtensorMap* m1p, const CUtensorM
         const int b = s % kInvSlots;
         const uint32_t dst = ring_s + (uint32_t)(b * Lay::SLOT * sizeof(S));
         const uint32_t bar = bar_s + 8 * b;
-        const int q0 = qbase + 4 * s;
+        const int q0 = qbase + SR * s;
         const bool l1 = s >= PRO_SLOTS;
         uint32_t bytes = 0;
         if (l1) bytes += (NL == 1 ? 4 : 3) * Lay::BYTES1;
@@ -271,9 +295,9 @@ __device__ __forceinline__ bool inv_body(const CUtensorMap* m1p, const CUtensorM
             failed = true;
             break;
         }
-        const int q0 = qbase + 4 * s;
+        const int q0 = qbase + SR * s;
         const bool l1 = s >= PRO_SLOTS;
-        if (hfast && inv_rows_interior(q0, NL, LAG, no_r))
+        if (hfast && inv_rows_interior(q0, SR, NL, LAG, no_r))
             w.template slot<false>(ring + b * Lay::SLOT, q0, l1);
         else
             w.template slot<true>(ring + b * Lay::SLOT, q0, l1);
@@ -296,12 +320,13 @@ __device__ __forceinline__ bool inv_body(const CUtensorMap* m1p, const CUtensorM
     return true;
 }
 
-// 16 warps per SM (128 registers) with 2 quadruple columns per lane, 8 with 4;
-// the plain non-separable steps (48 multiply-adds per quadruple) measured
-// faster with the register budget of 12 warps
+// 16 warps per SM (128 registers) with 2 quadruple columns per lane, 12 with
+// 4 (slots of 2 quadruple rows); the plain non-separable steps (48
+// multiply-adds per quadruple) measured faster with the register budget of 12
+// warps
 template <class S, int SCH, int NL, int Q1>
 __global__ void __launch_bounds__(kInvWarps * 32,
-                                  (Q1 <= 2 ? (SCH == SCH_NONSEP ? 12 : 16) : 8) / kInvWarps)
+                                  (Q1 <= 2 ? (SCH == SCH_NONSEP ? 12 : 16) : 12) / kInvWarps)
     inv_tma_kernel(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2,
                    const __grid_constant__ CUtensorMap ml, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -416,10 +441,13 @@ cudaError_t launch_inv_queue(int elem, int scheme, const BatchEntry* table, int 
     return cudaErrorInvalidValue;
 }
 
+int inv_slot_rows(int q1) { return q1 >= 4 ? 2 : 4; }
+
 size_t inv_tma_smem_bytes(int elem_bytes, int nl, int q1) {
     const int A = 16 / elem_bytes, E = 128 / elem_bytes;
     const int W1 = 32 * q1 + A, W2 = 32 * (q1 / 2) + A;
-    const int R1 = (4 * W1 + E - 1) / E * E, R2 = (2 * W2 + E - 1) / E * E;
+    const int sr = inv_slot_rows(q1);
+    const int R1 = (sr * W1 + E - 1) / E * E, R2 = ((sr / 2) * W2 + E - 1) / E * E;
     const int slot = nl == 1 ? 4 * R1 : 3 * R1 + 4 * R2;
     return (size_t)kInvWarps * kInvSlots * slot * elem_bytes + (size_t)kInvWarps * kInvSlots * 8;
 }
@@ -439,11 +467,6 @@ template <class T, int SCH>
 static cudaError_t inv_launch_nl(int nl, int q1, const CUtensorMap& m1, const CUtensorMap& m2,
                                  const CUtensorMap& ml, const FusedArgs& a, int grid,
                                  cudaStream_t st) {
-    if constexpr (sizeof(T) == 2) {  // 16-bit storage: 2 columns per lane
-        if (nl == 1) return inv_launch_one<T, SCH, 1, 2>(m1, m2, ml, a, grid, st);
-        if (nl == 2) return inv_launch_one<T, SCH, 2, 2>(m1, m2, ml, a, grid, st);
-        return cudaErrorInvalidValue;
-    }
     if (q1 == 2) {
         if (nl == 1) return inv_launch_one<T, SCH, 1, 2>(m1, m2, ml, a, grid, st);
         if (nl == 2) return inv_launch_one<T, SCH, 2, 2>(m1, m2, ml, a, grid, st);
@@ -508,8 +531,8 @@ cudaError_t launch_inv_tma(int elem, int scheme, int nl, int q1, const CUtensorM
     switch (elem) {
         case 0: return inv_launch_sch<float>(scheme, nl, q1, m1, m2, ml, a, grid, st);
         case 1: return inv_launch_sch<int>(scheme, nl, q1, m1, m2, ml, a, grid, st);
-        case 2: return inv_launch_sch<__half>(scheme, nl, 2, m1, m2, ml, a, grid, st);
-        case 3: return inv_launch_sch<__nv_bfloat16>(scheme, nl, 2, m1, m2, ml, a, grid, st);
+        case 2: return inv_launch_sch<__half>(scheme, nl, q1, m1, m2, ml, a, grid, st);
+        case 3: return inv_launch_sch<__nv_bfloat16>(scheme, nl, q1, m1, m2, ml, a, grid, st);
     }
     return cudaErrorInvalidValue;
 }

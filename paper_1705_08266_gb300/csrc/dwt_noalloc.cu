@@ -43,8 +43,9 @@ extern "C" dwt2d_status dwt2d_forward_noalloc(dwt2d_plan_t plan, const void* d_s
     // every check dwt2d_forward makes, before anything goes on the stream
     s = dwt::check_transform_args(plan, d_src, src_pitch_bytes, d_dst, dst_pitch_bytes, scratch, scale);
     if (s != DWT2D_OK) return s;
-    // the status word must start at zero; everything else is written before it is read
-    if (cudaMemsetAsync(scratch, 0, sizeof(int), reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    // the header (its first word is the status word) must start at zero;
+    // everything else is written before it is read
+    if (cudaMemsetAsync(scratch, 0, 256, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
         return DWT2D_ERR_CUDA;
     return dwt2d_forward(plan, d_src, src_pitch_bytes, d_dst, dst_pitch_bytes, scratch, scale, stream);
 }

@@ -28,13 +28,14 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 }
 
 // Wait until *flag >= target (acquire, GPU scope); give up after `budget`
-// clock cycles.  Spins with a short sleep between reads.
+// clock cycles.  Spins with a short sleep between reads.  The comparison is
+// modulo 2^32 (counters that grow over many calls may wrap).
 __device__ __forceinline__ bool wait_counter_bounded(const int* flag, int target, long long budget) {
     const long long t0 = clock64();
     for (;;) {
         int v;
         asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
-        if (v >= target) return true;
+        if ((int)((unsigned)v - (unsigned)target) >= 0) return true;
         if (clock64() - t0 > budget) return false;
         __nanosleep(256);
     }

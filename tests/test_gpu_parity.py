@@ -5,6 +5,7 @@ segments with ragged tails, odd sizes, axes of length 1 and 2.  CDF 9/7
 float32 must stay within 1e-5 * max|x| per level; reversible 5/3 int32 must be
 bit-exact for every scheme.
 """
+import ctypes
 import os
 
 import numpy as np
@@ -266,6 +267,8 @@ LAUNCH_OPTIONS = [
     {"fwd_cols_per_lane": 4, "fwd_short_tail": 2, "min_segment": 1, "fwd_warps_per_sm": 4000,
      "inv_short_tail": 2, "inv_warps_per_sm": 4000},
     {"fwd_cols_per_lane": 4, "fuse_first": 1, "fwd_seg_interleave": 1, "inv_seg_interleave": -1},
+    {"inv_cols_per_lane": 4, "inv_short_tail": -1},
+    {"programmatic_launch": -1},
 ]
 
 
@@ -305,3 +308,22 @@ def test_launch_options_give_the_same_bits(opts, wavelet, dtype):
         assert torch.equal(res[0][1], res[1][1]), (opts, h, w, levels, "inverse")
         if dtype != torch.float16:
             assert_forward_matches(res[0][0].numpy(), x, levels, wavelet, f"{h}x{w} L{levels}")
+
+
+def test_plans_sharing_a_workspace():
+    """Two different plans called alternately on one workspace, many times in
+    a row on one stream, give the bits of calls on fresh workspaces."""
+    shapes = [((2050, 3001), 6), ((1030, 2050), 5)]
+    plans = [D.Plan(h, w, lv, "cdf97", "nonsep_reduced") for (h, w), lv in shapes]
+    ws = torch.empty(max(p.workspace_bytes for p in plans), dtype=torch.uint8, device="cuda")
+    D.lib().dwt2d_workspace_init(ctypes.c_void_p(ws.data_ptr()), None)
+    xs = [device_image(make_input("cdf97", h, w, seed=h + w)) for (h, w), _lv in shapes]
+    refs = [p.forward(x) for p, x in zip(plans, xs)]  # each on its own fresh workspace
+    outs = [D.empty_image(x.shape[0], x.shape[1]) for x in xs]
+    for _ in range(5):
+        for p, x, o in zip(plans, xs, outs):
+            p.forward(x, o, ws)
+    torch.cuda.synchronize()
+    assert plans[0].status(ws) == 0
+    for o, r in zip(outs, refs):
+        assert torch.equal(o, r)
