@@ -155,6 +155,58 @@ struct FwdWarp {
     // block.  With q0 % SR == 0 the rows every level emits, and how LL rows
     // pair into the next level's quadruple rows, are fixed by the pipeline lag
     // alone.
+    // Level-2 input rows of the slot at q0: LL rows q0 - 2 .. q0 + SR - 3
+    // paired into quadruple rows q0/2 - 1 .. q0/2 + SR/2 - 2.
+    template <int R2>
+    __device__ __forceinline__ void pair_level1(const Block<T, Q1, SR>& b1, Block<T, Q2, R2>& b2) {
+        if constexpr (LAG == 2) {  // emitted rows q0-2 .. q0+SR-3
+#pragma unroll
+            for (int j = 0; j < R2; ++j) pair_rows<T, Q1>(b1.r[2 * j].c[0], b1.r[2 * j + 1].c[0], b2.r[j]);
+        } else {  // emitted rows q0-1 .. q0+SR-2; row q0-2 was kept from the last slot
+            pair_rows<T, Q1>(pend1, b1.r[0].c[0], b2.r[0]);
+#pragma unroll
+            for (int j = 1; j < R2; ++j) pair_rows<T, Q1>(b1.r[2 * j - 1].c[0], b1.r[2 * j].c[0], b2.r[j]);
+            copy_arr(pend1, b1.r[SR - 1].c[0]);
+        }
+    }
+
+    // Store the R2 level-2 rows a level-2 push of input rows from in2 emitted.
+    template <bool EDGE, int R2>
+    __device__ __forceinline__ void store_level2(const Block<T, Q2, R2>& b2, int in2) {
+        const int r2 = in2 - LAG;
+        if constexpr (!EDGE) {
+            S* hl = mallat + (long long)r2 * mpitch + (s2.g0 + s2.ne_c);
+            S* lh = hl + ((long long)s2.ne_r * mpitch - s2.ne_c);
+            S* lrow = ll + (long long)r2 * llpitch + s2.g0;
+#pragma unroll
+            for (int k = 0; k < R2; ++k) {
+                const bool ok = lane_ok && r2 + k >= s2.r_lo && r2 + k < s2.r_hi;
+                st_fast<S, T, Q2>(hl, b2.r[k].c[1], ok);
+                st_fast<S, T, Q2>(lh, b2.r[k].c[2], ok);
+                st_fast<S, T, Q2>(lh + s2.ne_c, b2.r[k].c[3], ok);
+                hl += mpitch;
+                lh += mpitch;
+                if constexpr (NL == 2) {
+                    st_fast<S, T, Q2>(lrow, b2.r[k].c[0], ok);
+                    lrow += llpitch;
+                }
+            }
+        } else {
+            S* base = mallat + (long long)r2 * mpitch + s2.g0;
+            const long long dlh = (long long)s2.ne_r * mpitch;
+            S* lrow = ll + (long long)r2 * llpitch + s2.g0;
+#pragma unroll
+            for (int k = 0; k < R2; ++k) {
+                store_details_at<S, T, Q2>(b2.r[k], r2 + k, s2, base, dlh, lane_ok);
+                base += mpitch;
+                if constexpr (NL == 2) {
+                    store_ll_at<S, T, Q2>(b2.r[k], r2 + k, s2, lrow, lane_ok, vec_ll);
+                    lrow += llpitch;
+                }
+            }
+        }
+    }
+
     template <bool EDGE>
     __device__ __forceinline__ void slot(const S* sm, int q0) {
         Block<T, Q1, SR> b1;
@@ -213,49 +265,10 @@ struct FwdWarp {
             // level-2 input rows q0/2 - 1 .. q0/2 + R2 - 2 = LL rows q0 - 2 .. q0 + SR - 3
             constexpr int R2 = SR / 2;
             Block<T, Q2, R2> b2;
-            if constexpr (LAG == 2) {  // emitted rows q0-2 .. q0+SR-3
-#pragma unroll
-                for (int j = 0; j < R2; ++j) pair_rows<T, Q1>(b1.r[2 * j].c[0], b1.r[2 * j + 1].c[0], b2.r[j]);
-            } else {  // emitted rows q0-1 .. q0+SR-2; row q0-2 was kept from the last slot
-                pair_rows<T, Q1>(pend1, b1.r[0].c[0], b2.r[0]);
-#pragma unroll
-                for (int j = 1; j < R2; ++j) pair_rows<T, Q1>(b1.r[2 * j - 1].c[0], b1.r[2 * j].c[0], b2.r[j]);
-                copy_arr(pend1, b1.r[SR - 1].c[0]);
-            }
+            pair_level1<R2>(b1, b2);
             const int in2 = q0 / 2 - 1;
             e2.template push<EDGE, R2>(b2, in2, x2);
-            const int r2 = in2 - LAG;
-            if constexpr (!EDGE) {
-                S* hl = mallat + (long long)r2 * mpitch + (s2.g0 + s2.ne_c);
-                S* lh = hl + ((long long)s2.ne_r * mpitch - s2.ne_c);
-                S* lrow = ll + (long long)r2 * llpitch + s2.g0;
-#pragma unroll
-                for (int k = 0; k < R2; ++k) {
-                    const bool ok = lane_ok && r2 + k >= s2.r_lo && r2 + k < s2.r_hi;
-                    st_fast<S, T, Q2>(hl, b2.r[k].c[1], ok);
-                    st_fast<S, T, Q2>(lh, b2.r[k].c[2], ok);
-                    st_fast<S, T, Q2>(lh + s2.ne_c, b2.r[k].c[3], ok);
-                    hl += mpitch;
-                    lh += mpitch;
-                    if constexpr (NL == 2) {
-                        st_fast<S, T, Q2>(lrow, b2.r[k].c[0], ok);
-                        lrow += llpitch;
-                    }
-                }
-            } else {
-                S* base = mallat + (long long)r2 * mpitch + s2.g0;
-                const long long dlh = (long long)s2.ne_r * mpitch;
-                S* lrow = ll + (long long)r2 * llpitch + s2.g0;
-#pragma unroll
-                for (int k = 0; k < R2; ++k) {
-                    store_details_at<S, T, Q2>(b2.r[k], r2 + k, s2, base, dlh, lane_ok);
-                    base += mpitch;
-                    if constexpr (NL == 2) {
-                        store_ll_at<S, T, Q2>(b2.r[k], r2 + k, s2, lrow, lane_ok, vec_ll);
-                        lrow += llpitch;
-                    }
-                }
-            }
+            store_level2<EDGE, R2>(b2, in2);
             if constexpr (NL >= 3) {
                 static_assert(Q1 >= 4, "three fused levels need 4 columns per lane");
                 Block<T, Q3, 1> b3;
