@@ -56,6 +56,9 @@ def parse():
                     help="time only the inverse of the headline workload (for profiling its kernels)")
     ap.add_argument("--size", type=int, default=8192,
                     help="image side (profiling runs use a smaller case; the metric is 8192)")
+    ap.add_argument("--scheme", default=None,
+                    help="time the workload with another lifting scheme (profiling runs; the metric "
+                         "is non-separable reduced)")
     return ap.parse_args()
 
 
@@ -300,9 +303,11 @@ def run_reference(args, ws, rank):
 
 
 def main():
-    global H, W
+    global H, W, HEADLINE_SCHEME
     args = parse()
     H = W = args.size
+    if args.scheme:
+        HEADLINE_SCHEME = args.scheme
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)

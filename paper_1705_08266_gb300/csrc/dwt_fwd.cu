@@ -305,6 +305,8 @@ __device__ __forceinline__ bool rows_interior(int q0, int sr, int nl, int lag, c
 // CTAs per SM the register budget is sized for: 16 warps (128 registers) with
 // 2 quadruple columns per lane; with 4, 12 warps (168 registers) for slots of
 // 2 quadruple rows, 8 for three fused levels.
+// (measured: 13-16 warps with 4 columns, at 128 registers and 32-60 bytes
+// of spills, were 2-20 % slower than 12 at 168 registers)
 template <int NL, int Q1>
 __host__ __device__ constexpr int fwd_min_blocks() {
     return (Q1 <= 2 ? 16 : (fwd_slot_quads<NL, Q1>() == 2 ? 12 : 8)) / kFwdWarps;
