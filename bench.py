@@ -388,7 +388,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
                 "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": f"fwd_fused_kernel<float, nonsep_reduced, {shapes[0][0]} levels, "
+                "kernel": f"fwd_fused_kernel<float, {HEADLINE_SCHEME}, {shapes[0][0]} levels, "
                           f"{shapes[0][1]} columns/lane> (launch {dom} of {launches}, {shapes[0][2]} warps)",
                 "kernel_ms": round(launch_ms[dom], 5),
                 "kernel_timing": "CUDA events around launch 0 of each step, second pass of K steps",
