@@ -346,7 +346,10 @@ typedef struct {
  * smallest row segment of a warp (quadruple rows of the last fused level;
  * default 2), and whether the batch's launches use programmatic stream
  * serialization (1 on, -1 or 0 off: measured neutral to 1 % slower for
- * batches).  Every warp of a launch streams the same number of rows. */
+ * batches).  Every warp of a launch streams the same number of rows.
+ * cols_per_lane: quadruple columns per lane at the first level of a launch
+ * (0 or 2: 2, a 128-pixel strip per warp; 4: a 256-pixel strip with half the
+ * strips' halo overlap; any other value is DWT2D_ERR_INVALID). */
 typedef struct {
     int32_t fuse_first, fuse_max, warps_per_sm, min_segment;
     int32_t programmatic_launch;
@@ -355,6 +358,7 @@ typedef struct {
                             counter; an item waits, bounded, until the level group it reads
                             is done); otherwise one launch per level group, direction,
                             storage type and fusion depth */
+    int32_t cols_per_lane;
 } dwt2d_tuning;
 
 /*

@@ -1,12 +1,14 @@
 """Autotuner for batched transforms (dwt2d_batch_*).
 
-A batch's launch shape has five knobs (dwt2d_tuning): levels fused in an
+A batch's launch shape has six knobs (dwt2d_tuning): levels fused in an
 image's first launch, levels fused per later launch (with the wavelet, this
 sets the halo each strip and segment recomputes), warps targeted per SM (how
 finely the rows are cut into warp segments, i.e. how many waves or queue
-items), the smallest segment, and the launch form (one launch per level group
+items), the smallest segment, the launch form (one launch per level group
 and kind, or one persistent launch per direction and storage type over a
-queue of work items).  The best setting depends on the mix of
+queue of work items) and the tile width (2 or 4 quadruple columns per lane:
+128- or 256-pixel strips, the wider with half the halo overlap per pixel but
+fewer strips to spread).  The best setting depends on the mix of
 image sizes and level counts, so the tuner times a small set of candidates on
 the batch itself (CUDA events, on the caller's buffers: the outputs are
 overwritten) and keeps the fastest.  Results are cached in a JSON file keyed
@@ -21,14 +23,20 @@ import json
 import os
 from typing import Callable, Iterable, Optional
 
-KNOBS = ("fuse_first", "fuse_max", "warps_per_sm", "min_segment", "persistent")
+KNOBS = ("fuse_first", "fuse_max", "warps_per_sm", "min_segment", "persistent", "cols_per_lane")
 
 CANDIDATES = [
-    {"fuse_first": ff, "fuse_max": 2, "warps_per_sm": w, "min_segment": m, "persistent": 0}
+    {"fuse_first": ff, "fuse_max": 2, "warps_per_sm": w, "min_segment": m, "persistent": 0,
+     "cols_per_lane": 2}
     for ff in (2, 1) for w in (12, 24, 32, 48) for m in (2, 8)
 ] + [
-    {"fuse_first": 2, "fuse_max": 2, "warps_per_sm": w, "min_segment": m, "persistent": 1}
-    for w in (24, 48, 96) for m in (2, 8)
+    {"fuse_first": 2, "fuse_max": 2, "warps_per_sm": w, "min_segment": 2, "persistent": 0,
+     "cols_per_lane": 4}
+    for w in (12, 24, 48)
+] + [
+    {"fuse_first": 2, "fuse_max": 2, "warps_per_sm": w, "min_segment": m, "persistent": 1,
+     "cols_per_lane": q}
+    for q in (2, 4) for w in (24, 48, 96) for m in (2, 8)
 ]
 
 

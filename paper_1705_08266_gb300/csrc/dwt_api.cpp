@@ -76,6 +76,7 @@ struct dwt2d_batch_s {
     };
     dwt2d_scheme scheme;
     bool pdl;  // launches with programmatic stream serialization
+    int q1;    // quadruple columns per lane of every launch (2 or 4)
     std::vector<dwt2d_batch_item> items;
     std::vector<dwt2d_plan_s*> plans;
     std::vector<size_t> region;             // workspace offset of each image's LL buffers
@@ -1275,8 +1276,11 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
         return DWT2D_ERR_UNSUPPORTED;
     dwt2d_tuning tun = {0, 0, 0, 0};
     if (tuning) tun = *tuning;
-    // the batched kernels run 2 quadruple columns per lane: up to 2 fused levels
+    // the batched kernels run 2 or 4 quadruple columns per lane and fuse up to 2 levels
     if (tun.fuse_max > 2 || tun.fuse_first > 2) return DWT2D_ERR_UNSUPPORTED;
+    if (tun.cols_per_lane != 0 && tun.cols_per_lane != 2 && tun.cols_per_lane != 4)
+        return DWT2D_ERR_INVALID;
+    const int q1 = tun.cols_per_lane == 4 ? 4 : 2;
     if (tun.fuse_max <= 0) tun.fuse_max = 2;
     const int wps = tun.warps_per_sm;
     tun.warps_per_sm = 0;  // the per-image share is set below
@@ -1285,6 +1289,7 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
     b->scheme = scheme;
     b->pdl = tun.programmatic_launch > 0;  // default off: measured neutral to 1 % slower for batches
     b->queue = tun.persistent > 0;
+    b->q1 = q1;
     b->items.assign(items, items + n);
     size_t off = kHeader;
     b->table_off = off;
@@ -1303,7 +1308,7 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
             delete b;
             return s;
         }
-        p->fwd_q1 = p->inv_q1 = 2;
+        p->fwd_q1 = p->inv_q1 = q1;
         b->plans.push_back(p);
     }
     // Launch list: phase k, then direction, storage type, fusion depth.  One
@@ -1343,7 +1348,7 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
                         FusedArgs a;
                         memset(&a, 0, sizeof(a));
                         int grid = 0;
-                        decompose(p, c.w0, c.rows, nl, c.rho, 2, 1, &a, &grid, 4);
+                        decompose(p, c.w0, c.rows, nl, c.rho, q1, 1, &a, &grid, 4);
                         c.nstrips = a.nstrips;
                         work += (long long)c.nstrips * c.rows;
                         min_segq = std::max(min_segq, p->min_segq);
@@ -1358,7 +1363,7 @@ dwt2d_status dwt2d_batch_create(dwt2d_batch_t* out, const dwt2d_batch_item* item
                         FusedArgs a;
                         memset(&a, 0, sizeof(a));
                         int grid = 0;
-                        decompose(p, c.w0, c.rows, nl, c.rho, 2, 1, &a, &grid, 4, segq);
+                        decompose(p, c.w0, c.rows, nl, c.rho, q1, 1, &a, &grid, 4, segq);
                         b->refs.push_back({c.i, k});
                         b->segq.push_back(segq);
                         warps += (long long)a.nstrips * a.nsegs;
@@ -1449,7 +1454,7 @@ static dwt2d_status batch_upload(dwt2d_batch_t b, void* d_ws, void* h_staging, s
                                          it.d_dst, it.dst_pitch_bytes / p->elem, wsb + b->region[i],
                                          err, 1, 1, &gl, b->segq[j]);
             if (s != DWT2D_OK) return s;
-            if (gl.path == 2 || gl.nl != L.nl) return DWT2D_ERR_INVALID;  // planned otherwise
+            if (gl.path == 2 || gl.nl != L.nl || gl.q1 != b->q1) return DWT2D_ERR_INVALID;  // planned otherwise
             BatchEntry& e = b->table[j];
             memcpy(e.m, gl.m, sizeof(e.m));
             e.args = gl.a;
@@ -1458,8 +1463,9 @@ static dwt2d_status batch_upload(dwt2d_batch_t b, void* d_ws, void* h_staging, s
         }
         // kernel attributes once, outside any capture
         const int sch = base_scheme(b->scheme);
-        const cudaError_t e = L.fwd ? launch_fwd_batched(L.elem_kind, sch, L.nl, nullptr, 0, 0, st, false)
-                                    : launch_inv_batched(L.elem_kind, sch, L.nl, nullptr, 0, 0, st, false);
+        const cudaError_t e =
+            L.fwd ? launch_fwd_batched(L.elem_kind, sch, L.nl, b->q1, nullptr, 0, 0, st, false)
+                  : launch_inv_batched(L.elem_kind, sch, L.nl, b->q1, nullptr, 0, 0, st, false);
         if (e != cudaSuccess) return DWT2D_ERR_CUDA;
     }
     // the tables go up from the caller's pinned staging buffer when given one
@@ -1502,10 +1508,10 @@ static dwt2d_status batch_upload(dwt2d_batch_t b, void* d_ws, void* h_staging, s
         q.items = first;
         if (first > (1LL << 30)) return DWT2D_ERR_INVALID;
         const int sch = base_scheme(b->scheme);
-        const cudaError_t e = q.fwd ? launch_fwd_queue(q.elem_kind, sch, nullptr, 0, 0, nullptr, nullptr,
-                                                       nullptr, 0, st)
-                                    : launch_inv_queue(q.elem_kind, sch, nullptr, 0, 0, nullptr, nullptr,
-                                                       nullptr, 0, st);
+        const cudaError_t e = q.fwd ? launch_fwd_queue(q.elem_kind, sch, b->q1, nullptr, 0, 0, nullptr,
+                                                       nullptr, nullptr, 0, st)
+                                    : launch_inv_queue(q.elem_kind, sch, b->q1, nullptr, 0, 0, nullptr,
+                                                       nullptr, nullptr, 0, st);
         if (e != cudaSuccess) return DWT2D_ERR_CUDA;
     }
     if (upload(b->qtable_off, b->qtable, b->table.size() * sizeof(BatchEntry)) != cudaSuccess)
@@ -1530,14 +1536,16 @@ dwt2d_status dwt2d_batch_launch(dwt2d_batch_t b, void* d_ws, void* stream) {
         // counters start at zero on every launch (a memset node in a captured graph)
         if (cudaMemsetAsync(heads, 0, b->counters_bytes, st) != cudaSuccess) return DWT2D_ERR_CUDA;
         const BatchEntry* qt = reinterpret_cast<const BatchEntry*>(wsb + b->qtable_off);
-        const long long resident = (long long)b->sms * 12;  // the queue kernels' register budget
         for (size_t qi = 0; qi < b->queues.size(); ++qi) {
             const auto& q = b->queues[qi];
+            // one wave: the warps the queue kernel's register budget keeps resident
+            const long long resident =
+                (long long)b->sms * (q.fwd ? fwd_queue_resident(b->q1) : inv_queue_resident(b->q1));
             const int grid = (int)std::min<long long>(q.items, resident);
             const cudaError_t e =
-                q.fwd ? launch_fwd_queue(q.elem_kind, sch, qt + q.first, q.count, (int)q.items,
+                q.fwd ? launch_fwd_queue(q.elem_kind, sch, b->q1, qt + q.first, q.count, (int)q.items,
                                          heads + qi, done, err, grid, st)
-                      : launch_inv_queue(q.elem_kind, sch, qt + q.first, q.count, (int)q.items,
+                      : launch_inv_queue(q.elem_kind, sch, b->q1, qt + q.first, q.count, (int)q.items,
                                          heads + qi, done, err, grid, st);
             if (e != cudaSuccess) return DWT2D_ERR_CUDA;
         }
@@ -1545,8 +1553,10 @@ dwt2d_status dwt2d_batch_launch(dwt2d_batch_t b, void* d_ws, void* stream) {
     }
     for (const auto& L : b->launches) {
         const cudaError_t e =
-            L.fwd ? launch_fwd_batched(L.elem_kind, sch, L.nl, table + L.first, L.count, L.grid, st, b->pdl)
-                  : launch_inv_batched(L.elem_kind, sch, L.nl, table + L.first, L.count, L.grid, st, b->pdl);
+            L.fwd ? launch_fwd_batched(L.elem_kind, sch, L.nl, b->q1, table + L.first, L.count, L.grid,
+                                       st, b->pdl)
+                  : launch_inv_batched(L.elem_kind, sch, L.nl, b->q1, table + L.first, L.count, L.grid,
+                                       st, b->pdl);
         if (e != cudaSuccess) return DWT2D_ERR_CUDA;
     }
     return DWT2D_OK;

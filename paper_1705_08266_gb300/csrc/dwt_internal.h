@@ -83,9 +83,13 @@ struct BatchEntry {
 // `total` work items of a queue (entries of one direction and storage type,
 // every level group, ordered by group) through the counter `head`; an item of
 // a later group first waits (bounded) until done[dep] reaches dep_items.
-cudaError_t launch_fwd_queue(int elem, int scheme, const BatchEntry* table, int n, int total,
+// q1: quadruple columns per lane (2 or 4) of every item in the queue.
+// Warps per SM that the queue kernels' register budget keeps resident.
+__host__ __device__ constexpr int fwd_queue_resident(int q1) { return q1 >= 4 ? 8 : 12; }
+__host__ __device__ constexpr int inv_queue_resident(int q1) { return q1 >= 4 ? 8 : 12; }
+cudaError_t launch_fwd_queue(int elem, int scheme, int q1, const BatchEntry* table, int n, int total,
                              int* head, int* done, int* err, int grid, cudaStream_t st);
-cudaError_t launch_inv_queue(int elem, int scheme, const BatchEntry* table, int n, int total,
+cudaError_t launch_inv_queue(int elem, int scheme, int q1, const BatchEntry* table, int n, int total,
                              int* head, int* done, int* err, int grid, cudaStream_t st);
 
 // Kernel-geometry constants of the streaming forward kernel.
@@ -100,15 +104,15 @@ constexpr int kFwdSlotRows = 8;     // image rows per TMA box (4 quadruple rows)
 int fwd_slot_rows(int nl, int q1);
 size_t fwd_smem_bytes(int elem_bytes, int nl, int q1);
 
-// Batched forward / inverse: entries of one element type, scheme and fusion
-// depth (1 or 2), 2 quadruple columns per lane; `grid` CTAs of kFwdWarps
-// (forward) or kInvTmaWarps (inverse) warps.
+// Batched forward / inverse: entries of one element type, scheme, fusion
+// depth (1 or 2) and quadruple columns per lane q1 (2 or 4); `grid` CTAs of
+// kFwdWarps (forward) or kInvTmaWarps (inverse) warps.
 // grid == 0 only sets the kernel's shared-memory attribute (done once, before
 // any stream capture), so a launch itself is a plain kernel launch.
-cudaError_t launch_fwd_batched(int elem, int scheme, int nl, const BatchEntry* table, int n, int grid,
-                               cudaStream_t st, bool pdl);
-cudaError_t launch_inv_batched(int elem, int scheme, int nl, const BatchEntry* table, int n, int grid,
-                               cudaStream_t st, bool pdl);
+cudaError_t launch_fwd_batched(int elem, int scheme, int nl, int q1, const BatchEntry* table, int n,
+                               int grid, cudaStream_t st, bool pdl);
+cudaError_t launch_inv_batched(int elem, int scheme, int nl, int q1, const BatchEntry* table, int n,
+                               int grid, cudaStream_t st, bool pdl);
 
 // Launch `kernel` on `st`; with `pdl` the grid is launched with programmatic
 // stream serialization (it may be scheduled while the previous kernel in the

@@ -51,7 +51,8 @@ class Tuning(ctypes.Structure):
     """dwt2d_tuning (0 = library default)."""
     _fields_ = [("fuse_first", ctypes.c_int32), ("fuse_max", ctypes.c_int32),
                 ("warps_per_sm", ctypes.c_int32), ("min_segment", ctypes.c_int32),
-                ("programmatic_launch", ctypes.c_int32), ("persistent", ctypes.c_int32)]
+                ("programmatic_launch", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("cols_per_lane", ctypes.c_int32)]
 
 
 class PlanOptions(ctypes.Structure):
@@ -306,9 +307,7 @@ class Batch:
                                dst.stride(0) * es)
         tun = None
         if tuning is not None:
-            tun = ctypes.byref(Tuning(*[int(tuning.get(k, 0)) for k in
-                                        ("fuse_first", "fuse_max", "warps_per_sm", "min_segment",
-                                         "programmatic_launch", "persistent")]))
+            tun = ctypes.byref(Tuning(*[int(tuning.get(k, 0)) for k, _t in Tuning._fields_]))
         self._h = ctypes.c_void_p()
         ws = ctypes.c_size_t()
         _check(L.dwt2d_batch_create(ctypes.byref(self._h), arr, len(self.jobs), SCHEMES[scheme], tun,

@@ -27,10 +27,13 @@ def main():
                 xd = D.empty_image(h, w, dt)
                 xd.copy_(torch.from_numpy(x).to(dt))
                 for scheme in ("separable", "nonsep", "nonsep_reduced"):
-                    for fuse in ("1", "2", "3"):
+                    for fuse, cols in (("1", 2), ("2", 2), ("3", 4), ("1", 4), ("2", 4)):
                         if fuse == "3" and dt == torch.float16:
                             continue
-                        plan = D.Plan(h, w, lv, wavelet, scheme, dt, options=dict(fuse_max=int(fuse)))
+                        opts = dict(fuse_max=int(fuse))
+                        if cols == 4:
+                            opts.update(fwd_cols_per_lane=4, inv_cols_per_lane=4)
+                        plan = D.Plan(h, w, lv, wavelet, scheme, dt, options=opts)
                         ws = plan.workspace()
                         c = plan.forward(xd, workspace=ws)
                         plan.inverse(c, workspace=ws)
@@ -38,7 +41,27 @@ def main():
                         runs += 1
                         if st != 0:
                             bad += 1
-                            print(f"status {st}: {h}x{w} L{lv} {wavelet} {dt} {scheme} fuse {fuse}")
+                            print(f"status {st}: {h}x{w} L{lv} {wavelet} {dt} {scheme} {opts}")
+    # every shape in one batch, forward and inverse, in both batched forms and
+    # at both tile widths
+    jobs = []
+    for i, (h, w, lv) in enumerate(SHAPES):
+        for inv in (0, 1):
+            x = torch.from_numpy(synth.image("cdf97", h, w, i)).to(torch.float32)
+            src = D.empty_image(h, w, torch.float32)
+            src.copy_(x)
+            jobs.append((src, D.empty_image(h, w, torch.float32), lv, "cdf97", inv))
+    for persistent in (0, 1):
+        for cols in (2, 4):
+            b = D.Batch(jobs, "nonsep_reduced", {"persistent": persistent, "cols_per_lane": cols})
+            ws = b.workspace()
+            b.upload(ws)
+            b.launch(ws)
+            st = b.status(ws)
+            runs += 1
+            if st != 0:
+                bad += 1
+                print(f"status {st}: batch persistent={persistent} cols={cols}")
     torch.cuda.synchronize()
     print(f"ok {runs}" if bad == 0 else f"failed {bad} of {runs}")
     return 1 if bad else 0

@@ -128,7 +128,8 @@ def test_batch_planning_launch_list(L):
 
 @pytest.mark.parametrize("case,status", [
     ("multipass_scheme", -2), ("fuse3", -2), ("same_buffer", -1), ("bad_pitch", -3),
-    ("bad_levels", -1), ("int_cdf", -2), ("empty", 0)])
+    ("bad_levels", -1), ("int_cdf", -2), ("empty", 0), ("cols4", 0), ("cols3", -1),
+    ("cols4_persistent", 0)])
 def test_batch_validation(L, case, status):
     items = [_item(64, 64, 2)]
     scheme, tun = 2, None
@@ -146,6 +147,8 @@ def test_batch_validation(L, case, status):
         items = [_item(64, 64, 2, wav=0, dt=1)]
     elif case == "empty":
         items = []
+    elif case.startswith("cols"):
+        tun = D.Tuning(cols_per_lane=int(case[4]), persistent=int(case.endswith("persistent")))
     st, b, ws = _batch(L, items, scheme, tun)
     assert st == status
     if st == 0:

@@ -276,6 +276,16 @@ def test_persistent_batch_equals_single_image_calls(scheme):
     _assert_same_as_single(jobs, scheme, f"persistent {scheme}")
 
 
+@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("scheme", ["nonsep_reduced", "separable"])
+def test_four_columns_per_lane_batch_equals_single_image_calls(scheme, persistent):
+    """256-pixel strips (4 quadruple columns per lane) in both batched forms:
+    the same bits as the single-image call."""
+    jobs, _ = _jobs(MIXED, 2028, scheme)
+    _run_batch(jobs, scheme, {"persistent": persistent, "cols_per_lane": 4})
+    _assert_same_as_single(jobs, scheme, f"4 columns per lane, persistent={persistent} {scheme}")
+
+
 def test_persistent_batch_graph_replay_on_new_inputs():
     """The queue counters are reset by the launch itself: a captured graph
     replays correctly, on new input contents, several times."""
@@ -313,8 +323,8 @@ def _c4_spec(seed=2017, n=256):
     return spec
 
 
-@pytest.mark.parametrize("persistent", [0, 1])
-def test_c4_batch_full_workload(persistent):
+@pytest.mark.parametrize("persistent,cols", [(0, 2), (1, 2), (1, 4)])
+def test_c4_batch_full_workload(persistent, cols):
     """The whole 256-image batching workload: every image bit for bit as the
     single-image call, and sampled coefficients of every image against the
     oracle (each from its dependency window)."""
@@ -328,10 +338,10 @@ def test_c4_batch_full_workload(persistent):
         src.copy_(torch.from_numpy(xh))
         jobs.append((src, D.empty_image(h, w, dt), lv, wav, 0))
         hosts.append(xh)
-    _run_batch(jobs, "nonsep_reduced", {"persistent": persistent})
-    _assert_same_as_single(jobs, "nonsep_reduced", f"C4 persistent={persistent}")
-    if persistent == 0:
-        return  # the oracle samples once: the two forms gave the same bits
+    _run_batch(jobs, "nonsep_reduced", {"persistent": persistent, "cols_per_lane": cols})
+    _assert_same_as_single(jobs, "nonsep_reduced", f"C4 persistent={persistent} cols={cols}")
+    if persistent == 0 or cols == 4:
+        return  # the oracle samples once: every form gave the same bits
     rng = np.random.default_rng(99)
     for i, ((src, dst, lv, wav, _i), xh) in enumerate(zip(jobs, hosts)):
         h, w = xh.shape
