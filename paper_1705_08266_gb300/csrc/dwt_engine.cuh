@@ -161,6 +161,45 @@ __device__ __forceinline__ void st_vec(S* p, const S (&v)[N]) {
     }
 }
 
+// st_vec with an L2 evict-last policy, for rows the next launch reads back:
+// the LL a forward launch hands on would otherwise leave the L2 under the
+// launch's detail-band stream (kept, its write-back also leaves the launch).
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_hint(void* p, unsigned short r, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(r), "l"(pol));
+}
+__device__ __forceinline__ void st_hint(void* p, unsigned int r, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(r), "l"(pol));
+}
+__device__ __forceinline__ void st_hint(void* p, uint2 r, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.b32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(r.x), "r"(r.y),
+                 "l"(pol));
+}
+__device__ __forceinline__ void st_hint(void* p, uint4 r, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(r.x),
+                 "r"(r.y), "r"(r.z), "r"(r.w), "l"(pol));
+}
+template <class S, int N>
+__device__ __forceinline__ void st_vec_keep(S* p, const S (&v)[N]) {
+    constexpr int B = N * (int)sizeof(S);
+    if constexpr (B <= 16) {
+        using R = typename RawVec<B>::type;
+        R r;
+        S* q = reinterpret_cast<S*>(&r);
+#pragma unroll
+        for (int j = 0; j < N; ++j) q[j] = v[j];
+        st_hint(p, r, l2_evict_last());
+    } else {
+        constexpr int H = N / 2;
+        st_vec_keep<S, H>(p, *reinterpret_cast<const S(*)[H]>(v));
+        st_vec_keep<S, H>(p + H, *reinterpret_cast<const S(*)[H]>(v + H));
+    }
+}
+
 // Per-level information of one lane (horizontal) and of the level (vertical).
 struct LevelCtx {
     unsigned right;  // bit j: column j has its right (even) neighbour inside the image

@@ -22,14 +22,17 @@
 namespace dwt {
 
 // Store Q consecutive values at p; `avail` columns remain inside the band.
+// keep: the next launch reads the values back (L2 evict-last).
 template <class S, class T, int Q>
-__device__ __forceinline__ void store_cols(S* p, const T (&v)[Q], int avail, bool vec) {
+__device__ __forceinline__ void store_cols(S* p, const T (&v)[Q], int avail, bool vec,
+                                           bool keep = false) {
     S w[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) w[j] = Storage<S>::st(v[j]);
     if (!store_ok(p, (avail < Q ? (avail > 0 ? avail : 0) : Q) * (int)sizeof(S))) return;
     if (vec && avail >= Q) {
-        st_vec<S, Q>(p, w);
+        if (keep) st_vec_keep<S, Q>(p, w);
+        else st_vec<S, Q>(p, w);
     } else {
 #pragma unroll
         for (int j = 0; j < Q; ++j)
@@ -41,11 +44,14 @@ __device__ __forceinline__ void store_cols(S* p, const T (&v)[Q], int avail, boo
 // band and p is vector aligned; ok = the lane stores and the row belongs to
 // the work item (one predicate, no branches per column).
 template <class S, class T, int Q>
-__device__ __forceinline__ void st_fast(S* p, const T (&v)[Q], bool ok) {
+__device__ __forceinline__ void st_fast(S* p, const T (&v)[Q], bool ok, bool keep = false) {
     S w[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) w[j] = Storage<S>::st(v[j]);
-    if (ok && store_ok(p, Q * (int)sizeof(S))) st_vec<S, Q>(p, w);
+    if (ok && store_ok(p, Q * (int)sizeof(S))) {
+        if (keep) st_vec_keep<S, Q>(p, w);
+        else st_vec<S, Q>(p, w);
+    }
 }
 
 // Per-level store state of one lane.
@@ -84,16 +90,16 @@ __device__ __forceinline__ void store_details(const Quads<T, Q>& a, int r, const
 // Row r's LL at `at` = ll + r * pitch + g0.
 template <class S, class T, int Q>
 __device__ __forceinline__ void store_ll_at(const Quads<T, Q>& a, int r, const StoreGeo& g, S* at,
-                                            bool lane_ok, bool vec) {
+                                            bool lane_ok, bool vec, bool keep) {
     if (!lane_ok || r < g.r_lo || r >= g.r_hi || r >= g.ne_r) return;
-    store_cols<S, T, Q>(at, a.c[0], g.ne_c - g.g0, vec);
+    store_cols<S, T, Q>(at, a.c[0], g.ne_c - g.g0, vec, keep);
 }
 
 template <class S, class T, int Q>
 __device__ __forceinline__ void store_ll(const Quads<T, Q>& a, int r, const StoreGeo& g, S* ll,
-                                         long long pitch, bool lane_ok, bool vec) {
+                                         long long pitch, bool lane_ok, bool vec, bool keep) {
     if (!lane_ok || r < g.r_lo || r >= g.r_hi || r >= g.ne_r) return;
-    store_cols<S, T, Q>(ll + (long long)r * pitch + g.g0, a.c[0], g.ne_c - g.g0, vec);
+    store_cols<S, T, Q>(ll + (long long)r * pitch + g.g0, a.c[0], g.ne_c - g.g0, vec, keep);
 }
 
 __device__ __forceinline__ StoreGeo make_geo(int h, int w, int g0, int Q, int r_lo, int r_hi,
@@ -152,6 +158,7 @@ struct FwdWarp {
     S* ll;
     long long mpitch, llpitch;
     bool lane_ok, vec_ll;
+    bool ll_keep;  // the next launch reads the LL back: store it L2 evict-last
     int lane;
 
     // One slot: level-1 input quadruple rows q0 .. q0+SR-1 (q0 a multiple of
@@ -191,7 +198,7 @@ struct FwdWarp {
                 hl += mpitch;
                 lh += mpitch;
                 if constexpr (NL == 2) {
-                    st_fast<S, T, Q2>(lrow, b2.r[k].c[0], ok);
+                    st_fast<S, T, Q2>(lrow, b2.r[k].c[0], ok, ll_keep);
                     lrow += llpitch;
                 }
             }
@@ -204,7 +211,7 @@ struct FwdWarp {
                 store_details_at<S, T, Q2>(b2.r[k], r2 + k, s2, base, dlh, lane_ok);
                 base += mpitch;
                 if constexpr (NL == 2) {
-                    store_ll_at<S, T, Q2>(b2.r[k], r2 + k, s2, lrow, lane_ok, vec_ll);
+                    store_ll_at<S, T, Q2>(b2.r[k], r2 + k, s2, lrow, lane_ok, vec_ll, ll_keep);
                     lrow += llpitch;
                 }
             }
@@ -245,7 +252,7 @@ struct FwdWarp {
                 hl += mpitch;
                 lh += mpitch;
                 if constexpr (NL == 1) {
-                    st_fast<S, T, Q1>(lrow, b1.r[k].c[0], ok);
+                    st_fast<S, T, Q1>(lrow, b1.r[k].c[0], ok, ll_keep);
                     lrow += llpitch;
                 }
             }
@@ -260,7 +267,7 @@ struct FwdWarp {
                 store_details_at<S, T, Q1>(b1.r[k], r1 + k, s1, base, dlh, lane_ok);
                 base += mpitch;
                 if constexpr (NL == 1) {
-                    store_ll_at<S, T, Q1>(b1.r[k], r1 + k, s1, lrow, lane_ok, vec_ll);
+                    store_ll_at<S, T, Q1>(b1.r[k], r1 + k, s1, lrow, lane_ok, vec_ll, ll_keep);
                     lrow += llpitch;
                 }
             }
@@ -287,7 +294,7 @@ struct FwdWarp {
                 }
                 e3.template push<EDGE, 1>(b3, in3, x3);
                 store_details<S, T, Q3>(b3.r[0], in3 - LAG, s3, mallat, mpitch, lane_ok);
-                store_ll<S, T, Q3>(b3.r[0], in3 - LAG, s3, ll, llpitch, lane_ok, vec_ll);
+                store_ll<S, T, Q3>(b3.r[0], in3 - LAG, s3, ll, llpitch, lane_ok, vec_ll, ll_keep);
             }
         }
     }
@@ -369,6 +376,7 @@ __device__ __forceinline__ bool fwd_body(const CUtensorMap* mapp, const FusedArg
     W.llpitch = a.ll_pitch;
     constexpr int QN = NL == 1 ? Q1 : (NL == 2 ? FW::Q2 : FW::Q3);
     W.vec_ll = (a.ll_pitch % QN) == 0;
+    W.ll_keep = a.ll_keep != 0;
     int no_r[3] = {0, 0, 0};
     bool hfast = true;
     {

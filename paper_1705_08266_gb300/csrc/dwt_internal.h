@@ -44,6 +44,7 @@ struct FusedArgs {
     int lane_lo, lane_hi;            // lanes that store
     int* err;                        // device status word (0 = ok)
     int pdl;                         // host: launch with programmatic stream serialization
+    int ll_keep;                     // forward: store the LL with an L2 evict-last policy
 };
 
 
