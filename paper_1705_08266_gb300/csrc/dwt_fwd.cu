@@ -9,7 +9,7 @@ template <class S, int SCH, int NL, int Q1>
 __global__ void __launch_bounds__(kFwdWarps * 32, fwd_min_blocks<NL, Q1>())
     fwd_fused_kernel(const __grid_constant__ CUtensorMap map, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    grid_dependency_sync();
+    grid_dependents_launch();  // the body waits for the previous grid after its setup
     const int wid = blockIdx.x * kFwdWarps + (threadIdx.x >> 5);
     if (wid >= a.nstrips * a.nsegs) return;
     fwd_body<S, SCH, NL, Q1>(&map, a, wid, smem_raw);

@@ -410,6 +410,10 @@ __device__ __forceinline__ bool fwd_body(const CUtensorMap* mapp, const FusedArg
     set_store_windows(a.mallat, a.mallat_elems * (long long)sizeof(S), a.ll,
                       a.ll_elems * (long long)sizeof(S), a.err);
 
+    // everything above came from the parameters: wait for the previous grid
+    // (its output is this launch's input) only now
+    grid_dependency_wait();
+
     // ---- TMA ring prologue
     const uint32_t ring_s = smem_u32(ring);
     const uint32_t bar_s = smem_u32(bars);

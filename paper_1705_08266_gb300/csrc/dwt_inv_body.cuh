@@ -251,6 +251,10 @@ __device__ __forceinline__ bool inv_body(const CUtensorMap* m1p, const CUtensorM
     const int nslots = nmain + PRO_SLOTS;
     const int qbase = qstart - SR * PRO_SLOTS;
 
+    // everything above came from the parameters: wait for the previous grid
+    // (its output is this launch's input) only now
+    grid_dependency_wait();
+
     const uint32_t ring_s = smem_u32(ring);
     const uint32_t bar_s = smem_u32(bars);
     auto issue = [&](int s) {

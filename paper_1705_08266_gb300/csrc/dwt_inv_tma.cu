@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(kInvWarps * 32,
     inv_tma_kernel(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2,
                    const __grid_constant__ CUtensorMap ml, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    grid_dependency_sync();
+    grid_dependents_launch();  // the body waits for the previous grid after its setup
     const int wid = blockIdx.x * kInvWarps + (threadIdx.x >> 5);
     if (wid >= a.nstrips * a.nsegs) return;
     inv_body<S, SCH, NL, Q1>(&m1, &m2, &ml, a, wid, smem_raw);

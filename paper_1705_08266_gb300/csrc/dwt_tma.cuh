@@ -113,6 +113,15 @@ __device__ __forceinline__ void grid_dependency_sync() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+// The two halves, for kernels that set up their registers (from parameters
+// only) between them: launch_dependents first, wait before the first global
+// access.
+__device__ __forceinline__ void grid_dependents_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 
 // About one second at GB300 clocks.
 constexpr long long kWaitBudget = 2000000000LL;
