@@ -719,32 +719,30 @@ def serving_variant(D, synth, dev, seconds: float = 10.0, rate: float = 2000.0):
         px += h * w
     import gc
 
-    srv = S.Server(budget_bytes=40 << 30, device=dev)
+    srv = S.Server(budget_bytes=40 << 30, device=dev, track_finished=True)
     # warm-up: module loading and kernel attributes outside the measurement
     warm = [srv.submit(r) for r in reqs[:32]]
     srv.run_until_idle(60)
     for t in warm:
         srv.release(t)
+    srv.take_finished()
     srv.reset_stats()
     # no collector pauses inside the timed loop (a serving process would tune it too)
     gc.collect()
     gc.disable()
     t0 = time.perf_counter()
     i = 0
-    pending = []
-    while i < n or pending:
+    outstanding = 0
+    while i < n or outstanding:
         now = time.perf_counter() - t0
         while i < n and arrivals[i] <= now:
-            pending.append(srv.submit(reqs[i], t_arrival=t0 + arrivals[i]))
+            srv.submit(reqs[i], t_arrival=t0 + arrivals[i])
+            outstanding += 1
             i += 1
         srv.poll()
-        still = []
-        for t in pending:
-            if t.finished():
-                srv.release(t)
-            else:
-                still.append(t)
-        pending = still
+        for t in srv.take_finished():  # release each result as soon as it completes
+            srv.release(t)
+            outstanding -= 1
     wall = time.perf_counter() - t0
     gc.enable()
     st = srv.stats()

@@ -152,7 +152,7 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> ctypes.c_void_p:
 
 def pitch_elems(width: int, dtype: torch.dtype) -> int:
     """Row pitch (elements) that makes every row start on a 16-byte boundary."""
-    es = torch.empty((), dtype=dtype).element_size()
+    es = dtype.itemsize
     return ((width * es + 15) // 16 * 16) // es
 
 
@@ -170,6 +170,21 @@ def as_pitched(t: torch.Tensor) -> torch.Tensor:
     out = empty_image(t.shape[0], t.shape[1], t.dtype, t.device)
     out.copy_(t)
     return out
+
+
+def workspace_bytes(height: int, width: int, levels: int, wavelet: str = "cdf97",
+                    scheme: str = "nonsep_reduced", dtype: Optional[torch.dtype] = None) -> int:
+    """Device workspace a default plan of this transform needs (dwt2d_plan,
+    then dwt2d_plan_destroy; no Python plan object)."""
+    L = lib()
+    if dtype is None:
+        dtype = torch.int32 if wavelet == "legall53" else torch.float32
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    _check(L.dwt2d_plan(ctypes.byref(h), height, width, levels, WAVELETS[wavelet], SCHEMES[scheme], 0,
+                        DTYPES[dtype], ctypes.byref(ws)), "dwt2d_plan")
+    L.dwt2d_plan_destroy(h)
+    return ws.value
 
 
 class Plan:

@@ -25,7 +25,9 @@ worker thread while the queue moves on.
 """
 from __future__ import annotations
 
+import collections
 import concurrent.futures as cf
+import contextlib
 import itertools
 import threading
 import time
@@ -146,16 +148,21 @@ class GpuExecutor:
         key = (req.height, req.width, req.levels, req.wavelet, req.dtype)
         n = self._ws_cache.get(key)
         if n is None:
-            plan = self.D.Plan(req.height, req.width, req.levels, req.wavelet, self.scheme, req.dtype)
-            n = plan.workspace_bytes
+            n = self.D.workspace_bytes(req.height, req.width, req.levels, req.wavelet, self.scheme,
+                                       req.dtype)
             if len(self._ws_cache) > 65536:
                 self._ws_cache.clear()
             self._ws_cache[key] = n
         return n
 
+    def allocating(self):
+        """Context for the allocations of the batch being formed: blocks owned
+        by its stream (entered once per batch, not per allocation)."""
+        return torch.cuda.stream(self.stream)
+
     def empty(self, h, w, dtype):
-        with torch.cuda.stream(self.stream):  # blocks owned by the batch's stream
-            return self.D.empty_image(h, w, dtype, self.device)
+        # called inside allocating(): the current stream is the batch's
+        return self.D.empty_image(h, w, dtype, self.device)
 
     def pitched(self, t: torch.Tensor) -> bool:
         es = t.element_size()
@@ -203,7 +210,8 @@ class Server:
 
     def __init__(self, budget_bytes: int = 40 << 30, executor=None, max_batch: int = 256,
                  max_inflight: int = 4, allocator: Optional[Callable] = None, loader_threads: int = 4,
-                 clock: Callable[[], float] = time.perf_counter, **executor_args):
+                 clock: Callable[[], float] = time.perf_counter, track_finished: bool = False,
+                 **executor_args):
         self.budget = int(budget_bytes)
         self.ex = executor if executor is not None else GpuExecutor(**executor_args)
         self.max_batch = max_batch
@@ -212,10 +220,12 @@ class Server:
         self.clock = clock
         self.in_use = 0
         self.peak = 0
-        self.queue: List[Ticket] = []
+        self.queue = collections.deque()  # of Ticket, arrival order
         self.inflight = []  # (handle, [tickets])
         # finished requests are counted, not kept (the client holds its tickets)
         self.counts = {DONE: 0, FAILED: 0, CANCELLED: 0, REJECTED: 0}
+        # tickets finished since take_finished() (kept only when asked for)
+        self._finished = collections.deque() if track_finished else None
         self.latencies: List[float] = []
         self._ids = itertools.count()
         self._lock = threading.Lock()
@@ -267,6 +277,18 @@ class Server:
                 return True
         self._finish(t, CANCELLED, "cancelled")
         return True
+
+    def take_finished(self) -> List[Ticket]:
+        """The tickets that finished (any final state) since the last call, in
+        the order they finished: a client releases results without scanning
+        every ticket it holds."""
+        if self._finished is None:
+            raise RuntimeError("Server(track_finished=True) keeps the finished tickets")
+        out = []
+        with self._lock:
+            while self._finished:
+                out.append(self._finished.popleft())
+        return out
 
     def release(self, t: Ticket) -> None:
         """The client is done with a resident result: return its memory."""
@@ -339,7 +361,7 @@ class Server:
     # ---- internals
     def _need(self, req: Request):
         """(resident output bytes, bytes held only while the kernels run)."""
-        es = torch.empty((), dtype=req.dtype).element_size()
+        es = req.dtype.itemsize
         img = req.height * ((req.width * es + 15) // 16 * 16)
         tmp = self.ex.workspace_bytes(req) + 4 * TABLE_ENTRY_BYTES
         data = req.data
@@ -387,21 +409,41 @@ class Server:
             self.counts[state] = self.counts.get(state, 0) + 1
             if state == DONE:
                 self.latencies.append(t.t_done - t.t_submit)
+            if self._finished is not None:
+                self._finished.append(t)
         t._event.set()
 
     def admit_and_launch(self):
         picked = []
         with self._lock:
-            for t in self.queue:
-                # arrival order: nobody overtakes a request waiting for memory
-                if len(picked) == self.max_batch or self.in_use + t.reserved > self.budget:
-                    break
+            q = self.queue
+            # arrival order: nobody overtakes a request waiting for memory
+            while q and len(picked) < self.max_batch and self.in_use + q[0].reserved <= self.budget:
+                t = q.popleft()
                 self._reserve(t.reserved)
                 picked.append(t)
-            self.queue = self.queue[len(picked):]
         if not picked:
             return
         jobs, ok = [], []
+        ctx = getattr(self.ex, "allocating", None)
+        with (ctx() if ctx is not None else contextlib.nullcontext()):
+            self._allocate(picked, jobs, ok)
+        if not ok:
+            return
+        try:
+            handle = self.ex.launch(jobs)
+        except Exception as e:
+            for t in ok:
+                self._unreserve(t)
+                self._finish(t, FAILED, f"launch failed: {e!r}")
+            return
+        self.batches += 1
+        self.batch_sizes.append(len(ok))
+        self.inflight.append((handle, ok))
+
+    def _allocate(self, picked, jobs, ok):
+        """Inputs (copied in if not resident and pitched) and outputs of the
+        picked requests; a refused allocation fails that request only."""
         for t in picked:
             r = t.request
             try:
@@ -421,18 +463,6 @@ class Server:
             t.t_start = self.clock()
             jobs.append((src, out, r.levels, r.wavelet, int(r.inverse)))
             ok.append(t)
-        if not ok:
-            return
-        try:
-            handle = self.ex.launch(jobs)
-        except Exception as e:
-            for t in ok:
-                self._unreserve(t)
-                self._finish(t, FAILED, f"launch failed: {e!r}")
-            return
-        self.batches += 1
-        self.batch_sizes.append(len(ok))
-        self.inflight.append((handle, ok))
 
     def retire(self) -> int:
         n = 0

@@ -4,6 +4,7 @@ import ctypes
 import os
 
 import pytest
+import torch
 
 from paper_1705_08266_gb300 import build as B
 from paper_1705_08266_gb300 import dwt2d as D
@@ -205,3 +206,11 @@ def test_plan_launch_info_reports_the_chosen_shapes(L):
                   options={"fwd_cols_per_lane": 4}).launch_info()[0][1] == 4
     with pytest.raises(D.DwtError):
         D.Plan(512, 512, 2, "cdf97", "nonsep_multipass").launch_info()
+
+
+@pytest.mark.parametrize("h,w,lv,wav,dt", [(1080, 1920, 5, "cdf97", torch.float32),
+                                           (77, 3001, 2, "legall53", torch.int32),
+                                           (4096, 512, 6, "cdf97", torch.float16)])
+def test_workspace_bytes_helper_matches_plan(h, w, lv, wav, dt):
+    assert D.workspace_bytes(h, w, lv, wav, "nonsep_reduced", dt) == \
+        D.Plan(h, w, lv, wav, "nonsep_reduced", dt).workspace_bytes

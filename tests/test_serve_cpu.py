@@ -247,3 +247,38 @@ def test_counts_exact_with_concurrent_loader_failures():
     st = srv.stats()
     assert st["completed"] == 0 and st["p99_s"] is None
     srv.close()
+
+
+def test_take_finished_hands_each_ticket_out_once():
+    """Finished tickets (done, rejected) come out of take_finished once each,
+    in the order they finished; without tracking the call is refused."""
+    srv = S.Server(budget_bytes=1 << 30, executor=FakeExecutor(lag=1), track_finished=True)
+    bad = srv.submit(req(h=0))  # malformed: rejected at submit
+    ts = [srv.submit(req(fill=float(i))) for i in range(6)]
+    got = srv.take_finished()
+    assert got == [bad] and bad.state == S.REJECTED
+    seen = []
+    for _ in range(50):
+        srv.poll()
+        seen += srv.take_finished()
+        if len(seen) == len(ts):
+            break
+    assert sorted(t.id for t in seen) == sorted(t.id for t in ts)
+    assert all(t.state == S.DONE for t in seen)
+    assert [t.t_done for t in seen] == sorted(t.t_done for t in seen)
+    assert srv.take_finished() == []
+    for t in seen:
+        srv.release(t)
+    assert srv.in_use == 0
+    with pytest.raises(RuntimeError):
+        S.Server(budget_bytes=1 << 30, executor=FakeExecutor()).take_finished()
+
+
+def test_queue_admits_in_arrival_order_under_backlog():
+    """A backlog longer than one batch drains in arrival order, max_batch at a time."""
+    ex = FakeExecutor()
+    srv = S.Server(budget_bytes=1 << 30, executor=ex, max_batch=4, max_inflight=1)
+    ts = [srv.submit(req(fill=float(i))) for i in range(10)]
+    assert srv.run_until_idle(5)
+    assert ex.launched == [4, 4, 2]
+    assert [t.t_start for t in ts] == sorted(t.t_start for t in ts)
