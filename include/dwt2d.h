@@ -212,7 +212,7 @@ dwt2d_status dwt2d_inverse(dwt2d_plan_t plan, const void* d_src, int64_t src_pit
  *   by band as its input rows arrive, and the finished detail bands come back
  *   on a second internal stream while later bands still go in (the plan owns
  *   the two streams; a plan's _host calls must not overlap each other; the
- *   band count is DWT2D_HOST_BANDS at plan creation, default 8).  The
+ *   band count is the plan option host_bands, default 8).  The
  *   inverse does the same the other way round: the coarse levels' top-left
  *   region goes in first, the finest level group runs by row bands as their
  *   detail bands arrive, and finished image rows come back meanwhile.
