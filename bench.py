@@ -602,9 +602,9 @@ def precision_variants(D, synth, dev, stream):
 def batch_variants(D, synth, dev, stream):
     """Batched forward transforms: 256 images, H and W uniform on 65..4096,
     levels uniform on 1..6, 75% CDF 9/7 float32 and 25% LeGall 5/3 int32
-    (seed 2017).  One batch (eager, replayed from a CUDA graph, and with the
-    autotuned launch shape) against one dwt2d_forward call per image (eager and
-    captured in one CUDA graph)."""
+    (seed 2017).  One batch (eager and replayed from a CUDA graph, in the
+    table and the persistent form and with the autotuned launch shape) against
+    one dwt2d_forward call per image (eager and captured in one CUDA graph)."""
     from paper_1705_08266_gb300 import autotune
 
     rng = np.random.default_rng(2017)
@@ -686,6 +686,18 @@ def batch_variants(D, synth, dev, stream):
     ms = time_calls(fn, iters, stream)
     res["batch_autotuned"] = {"ms": round(ms, 4), "gpx_s": round(px / ms / 1e6, 1), "tuning": best,
                               "launches": tb.info()[0]}
+    # the autotuned batch captured in a CUDA graph (its launches, and the
+    # queue-counter memset of the persistent form, replayed as one graph)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        fn()
+    with torch.cuda.stream(stream):
+        for _ in range(warm):
+            g.replay()
+        ms = time_calls(g.replay, iters, stream)
+    res["batch_autotuned_graph"] = {"ms": round(ms, 4), "gpx_s": round(px / ms / 1e6, 1)}
+    assert tb.status(tws, stream=stream) == 0
+    del g
     torch.cuda.synchronize()
     return res
 
