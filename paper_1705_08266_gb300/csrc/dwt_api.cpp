@@ -735,9 +735,10 @@ static dwt2d_status plan_create(dwt2d_plan_t* out, int32_t height, int32_t width
         h = (h + 1) / 2;
         w = (w + 1) / 2;
     }
-    // level groups: the first launch fuses DWT2D_FUSE_FIRST levels (default 2),
-    // later launches up to DWT2D_FUSE (default 2; 3 needs 4 columns per lane,
-    // which measured slower) each
+    // level groups: the first launch fuses fuse_first levels (default 2), later
+    // launches up to fuse_max (default 2; 3 needs 4 columns per lane, which
+    // measured slower) each; the shorter group comes last (5 levels: 2 + 2 + 1
+    // measured faster than 2 + 1 + 2 both ways)
     int maxf = tuning && tuning->fuse_max > 0 ? tuning->fuse_max : opt(o.fuse_max, 2);
     if (maxf < 1) maxf = 1;
     if (maxf > kMaxFused) maxf = kMaxFused;
