@@ -165,23 +165,25 @@ __device__ __forceinline__ void st_vec(S* p, const S (&v)[N]) {
 // the LL a forward launch hands on would otherwise leave the L2 under the
 // launch's detail-band stream (kept, its write-back also leaves the launch).
 __device__ __forceinline__ uint64_t l2_evict_last() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    uint64_t pol;  // a pure value: the compiler may compute it once
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
+// (the "memory" clobbers keep these stores ordered with every other memory
+// access of the thread, as plain stores are)
 __device__ __forceinline__ void st_hint(void* p, unsigned short r, uint64_t pol) {
-    asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(r), "l"(pol));
+    asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(r), "l"(pol) : "memory");
 }
 __device__ __forceinline__ void st_hint(void* p, unsigned int r, uint64_t pol) {
-    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(r), "l"(pol));
+    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(r), "l"(pol) : "memory");
 }
 __device__ __forceinline__ void st_hint(void* p, uint2 r, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.v2.b32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(r.x), "r"(r.y),
-                 "l"(pol));
+                 "l"(pol) : "memory");
 }
 __device__ __forceinline__ void st_hint(void* p, uint4 r, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(r.x),
-                 "r"(r.y), "r"(r.z), "r"(r.w), "l"(pol));
+                 "r"(r.y), "r"(r.z), "r"(r.w), "l"(pol) : "memory");
 }
 template <class S, int N>
 __device__ __forceinline__ void st_vec_keep(S* p, const S (&v)[N]) {
@@ -198,6 +200,18 @@ __device__ __forceinline__ void st_vec_keep(S* p, const S (&v)[N]) {
         st_vec_keep<S, H>(p, *reinterpret_cast<const S(*)[H]>(v));
         st_vec_keep<S, H>(p + H, *reinterpret_cast<const S(*)[H]>(v + H));
     }
+}
+
+// Batched kernels: the last table entry whose first_warp <= g (entries sorted
+// by first_warp, n >= 1).
+__device__ __forceinline__ int find_entry(const BatchEntry* __restrict__ table, int n, int g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (table[mid].first_warp <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // Per-level information of one lane (horizontal) and of the level (vertical).

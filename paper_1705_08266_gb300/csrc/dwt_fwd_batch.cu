@@ -7,17 +7,6 @@
 
 namespace dwt {
 
-// Binary search: the last entry with first_warp <= g.
-__device__ __forceinline__ int find_entry(const BatchEntry* __restrict__ table, int n, int g) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (table[mid].first_warp <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 // Many images in one launch: warp w of the grid works on entry i with
 // first[i] <= w < first[i + 1] of a table in device memory.  The arguments
 // come from registers instead of the constant bank, so the kernel gets the

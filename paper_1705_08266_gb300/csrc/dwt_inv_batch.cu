@@ -6,16 +6,6 @@
 
 namespace dwt {
 
-__device__ __forceinline__ int inv_find_entry(const BatchEntry* __restrict__ table, int n, int g) {
-    int lo = 0, hi = n - 1;  // last entry with first_warp <= g
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (table[mid].first_warp <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 // arguments in registers (not the constant bank): 12 warps per SM
 template <class S, int SCH, int NL, int Q1>
 __global__ void __launch_bounds__(kInvWarps * 32, 12 / kInvWarps)
@@ -23,7 +13,7 @@ __global__ void __launch_bounds__(kInvWarps * 32, 12 / kInvWarps)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     grid_dependency_sync();
     const int gw = blockIdx.x * kInvWarps + (threadIdx.x >> 5);
-    const BatchEntry& e = table[inv_find_entry(table, n, gw)];
+    const BatchEntry& e = table[find_entry(table, n, gw)];
     const int wid = gw - e.first_warp;
     const FusedArgs a = e.args;  // registers: the body's stores cannot alias it
     if (wid < 0 || wid >= a.nstrips * a.nsegs) return;
@@ -48,7 +38,7 @@ __global__ void __launch_bounds__(kInvWarps * 32, inv_queue_resident(Q1) / kInvW
         if (lane == 0) g = atomicAdd(head, 1);
         g = __shfl_sync(kFull, g, 0);
         if (g >= total) break;
-        const BatchEntry& e = table[inv_find_entry(table, n, g)];
+        const BatchEntry& e = table[find_entry(table, n, g)];
         const FusedArgs a = e.args;
         const int wid = g - e.first_warp;
         bool ok = true;
