@@ -429,6 +429,17 @@ __device__ __forceinline__ bool fwd_body(const CUtensorMap* mapp, const FusedArg
     }
     __syncwarp();
 
+    // the border-free slots form one run [si0, si1): the test holds from some
+    // slot on (rows far enough from the top) and up to some slot (clear of the
+    // bottom), so two scans find it instead of one test per slot
+    int si0 = nslots, si1 = nslots;
+    if (hfast) {
+        si0 = 0;
+        while (si0 < nslots && !rows_interior(qstart + SR * si0, SR, NL, RHO, no_r)) ++si0;
+        si1 = nslots;
+        while (si1 > si0 && !rows_interior(qstart + SR * (si1 - 1), SR, NL, RHO, no_r)) --si1;
+    }
+
     bool failed = false;
     int s = 0;
     for (; s < nslots; ++s) {
@@ -439,7 +450,7 @@ __device__ __forceinline__ bool fwd_body(const CUtensorMap* mapp, const FusedArg
             break;
         }
         const int q0 = qstart + SR * s;
-        if (hfast && rows_interior(q0, SR, NL, RHO, no_r))
+        if (s >= si0 && s < si1)
             W.template slot<false>(ring + b * kSlotElems, q0);
         else
             W.template slot<true>(ring + b * kSlotElems, q0);

@@ -293,6 +293,15 @@ __device__ __forceinline__ bool inv_body(const CUtensorMap* m1p, const CUtensorM
     }
     __syncwarp();
 
+    // the border-free slots form one run [si0, si1) (see the forward body)
+    int si0 = nslots, si1 = nslots;
+    if (hfast) {
+        si0 = 0;
+        while (si0 < nslots && !inv_rows_interior(qbase + SR * si0, SR, NL, LAG, no_r)) ++si0;
+        si1 = nslots;
+        while (si1 > si0 && !inv_rows_interior(qbase + SR * (si1 - 1), SR, NL, LAG, no_r)) --si1;
+    }
+
     bool failed = false;
     int s = 0;
     for (; s < nslots; ++s) {
@@ -304,7 +313,7 @@ __device__ __forceinline__ bool inv_body(const CUtensorMap* m1p, const CUtensorM
         }
         const int q0 = qbase + SR * s;
         const bool l1 = s >= PRO_SLOTS;
-        if (hfast && inv_rows_interior(q0, SR, NL, LAG, no_r))
+        if (s >= si0 && s < si1)
             w.template slot<false>(ring + b * Lay::SLOT, q0, l1);
         else
             w.template slot<true>(ring + b * Lay::SLOT, q0, l1);
