@@ -71,7 +71,6 @@ class Ticket:
     reserved: int = 0          # bytes counted against the budget
     reserved_out: int = 0      # the part that stays resident with the result
     _src: Optional[torch.Tensor] = field(default=None, repr=False)
-    _event: threading.Event = field(default_factory=threading.Event, repr=False)
 
     @property
     def latency(self) -> float:
@@ -411,7 +410,6 @@ class Server:
                 self.latencies.append(t.t_done - t.t_submit)
             if self._finished is not None:
                 self._finished.append(t)
-        t._event.set()
 
     def admit_and_launch(self):
         picked = []
