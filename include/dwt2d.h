@@ -342,7 +342,8 @@ typedef struct {
 /* Tuning knobs (0 = library default): levels fused in the first launch of an
  * image (1 or 2; default 2), at most per later launch (1 or 2; default 2),
  * warps per SM that the rows of one launch are cut into (default 48; the
- * batched kernels keep 12 warps per SM resident, so 48 is four waves), the
+ * batched kernels keep 12 warps per SM resident, 8 for the persistent form
+ * at 4 columns per lane, so 48 is four or six waves), the
  * smallest row segment of a warp (quadruple rows of the last fused level;
  * default 2), and whether the batch's launches use programmatic stream
  * serialization (1 on, -1 or 0 off: measured neutral to 1 % slower for
